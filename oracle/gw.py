@@ -175,7 +175,7 @@ def g_minus_tau(G):
 # --------------------------------------------------------------------------
 # P0, P, Sigma
 # --------------------------------------------------------------------------
-def polarization(G, V, nk, s=2, loop_sign=+1):
+def polarization(G, V, nk, s=2, loop_sign=+1, qs=None):
     """Bare bubble P0^q_{QQ'}(tau) of Eq. (P0) for every q of the mesh.
 
     P0^q_{QQ'}(tau) = loop_sign (s/N_k) sum_k sum_{abcd}
@@ -184,13 +184,14 @@ def polarization(G, V, nk, s=2, loop_sign=+1):
         X1(Q)_{ca}  = sum_d G^k_{cd}(-tau) V^{k,k+q}_{da}(Q),
         X2(Q')_{ac} = sum_b G^{k+q}_{ab}(tau) V^{k+q,k}_{bc}(Q'),
         P0_{QQ'}   += sum_{ca} X1(Q)_{ca} X2(Q')_{ac}.
+    ``qs`` restricts the evaluation to a list of q (other entries stay zero).
     """
     Vf = as_vfun(V)
     Nk, nt, nao, _ = G.shape
     Gm = g_minus_tau(G)
     naux = Vf(0, 0).shape[0]
     P0 = np.zeros((Nk, nt, naux, naux), dtype=np.complex128)
-    for q in range(Nk):
+    for q in (range(Nk) if qs is None else qs):
         for k in range(Nk):
             kq = kadd(nk, k, q)
             Vkq = Vf(k, kq)  # [Q][d][a]
@@ -227,7 +228,7 @@ def screened_interaction(P0_tau, TB, TBbar):
     return to_matsubara(Pw, TBbar), P0w, Pw
 
 
-def self_energy(G, P, V, nk):
+def self_energy(G, P, V, nk, ks=None):
     """Dynamic GW self-energy of Eq. (sigma) for every k of the mesh.
 
     Sigma^k_ij(tau) = -(1/N_k) sum_q sum_ab sum_QQ'
@@ -236,12 +237,13 @@ def self_energy(G, P, V, nk):
         X1(Q)_{ib}  = sum_a V^{k,k-q}_{ia}(Q) G^{k-q}_{ab}(tau),
         X2(Q')_{ib} = sum_Q X1(Q)_{ib} P^q_{QQ'}(tau),
         Sigma_ij   += sum_{Q' b} X2(Q')_{ib} V^{k-q,k}_{bj}(Q').
+    ``ks`` restricts the evaluation to a list of k (other entries stay zero).
     """
     Vf = as_vfun(V)
     Nk, nt, nao, _ = G.shape
     naux = P.shape[-1]
     Sig = np.zeros_like(G)
-    for k in range(Nk):
+    for k in (range(Nk) if ks is None else ks):
         for q in range(Nk):
             kmq = ksub(nk, k, q)
             V1 = Vf(k, kmq)  # [Q][i][a]

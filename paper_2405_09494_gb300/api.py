@@ -1,0 +1,123 @@
+"""Session: one library context for one workload, with its inputs loaded.
+
+Marshalling only: it turns a workload description and the seeded synthetic
+inputs into the C-ABI calls of :mod:`paper_2405_09494_gb300.sgw`, and
+allocates the caller-owned device buffers with PyTorch.  Every step of the
+method runs inside the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sgw, synth
+from .configs import Config
+
+
+def structure_arrays(cfg: Config):
+    """Crystal description for sgw_build_irrep_basis (from the workload definition)."""
+    ops = synth.space_group(cfg.structure)
+    rot = np.stack([R for R, _ in ops])
+    tra = np.stack([v for _, v in ops])
+    if cfg.structure == "none":
+        return np.eye(3), np.zeros((1, 3)), rot, tra, [0] * cfg.nao, [0] * cfg.naux
+    return synth.FCC, synth.atom_positions(cfg.structure), rot, tra, list(cfg.ao_shells), list(cfg.aux_shells)
+
+
+class Session:
+    def __init__(self, cfg: Config, precision: int = sgw.SGW_FP64, device: str = "cuda:0", system=None,
+                 load_v: bool = True):
+        import torch
+
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.sys = system if system is not None else synth.System(cfg)
+        self.ctx = sgw.sgw_create(cfg.nk, cfg.nao, cfg.naux, cfg.ntau, cfg.mats_f, cfg.mats_b, cfg.beta, cfg.n_elec,
+                                  cfg.spin, cfg.loop_sign, precision)
+        lat, pos, rot, tra, aos, axs = structure_arrays(cfg)
+        self.layout = sgw.sgw_build_irrep_basis(self.ctx, lat, pos, rot, tra, aos, axs)
+        L = self.layout
+        self.wedge, self.rep, self.op = sgw.sgw_get_wedge(self.ctx, L.nkpts, L.nwedge)
+        self.pairs = [sgw.sgw_get_pairs(self.ctx, w, L.npairs) for w in (0, 1)]
+        H0 = torch.from_numpy(np.ascontiguousarray(self.sys.H0)).to(self.device)
+        S = torch.from_numpy(np.ascontiguousarray(self.sys.S)).to(self.device)
+        sgw.sgw_load_one_body(self.ctx, H0, S)
+        if load_v:
+            self.load_v()
+
+    def load_v(self, chunk: int = 64):
+        torch = self.torch
+        cfg = self.cfg
+        for which in (0, 1):
+            k1, k2 = self.pairs[which]
+            n = len(k1)
+            for p0 in range(0, n, chunk):
+                p1 = min(n, p0 + chunk)
+                blk = np.stack([self.sys.V(int(a), int(b)) for a, b in zip(k1[p0:p1], k2[p0:p1])])
+                t = torch.from_numpy(blk).to(self.device)
+                sgw.sgw_load_v(self.ctx, which, p0, p1 - p0, t)
+                torch.cuda.synchronize(self.device)
+        del cfg
+
+    # ---- buffers ----------------------------------------------------------
+    def zeros(self, *shape):
+        return self.torch.zeros(*shape, dtype=self.torch.complex128, device=self.device)
+
+    def g_series(self, nt=None):
+        return self.zeros(nt or self.cfg.ntau, self.layout.g_elems)
+
+    def p_series(self, nt=None):
+        return self.zeros(nt or self.cfg.ntau, self.layout.p_elems)
+
+    # ---- steps --------------------------------------------------------------
+    def g0(self):
+        G = self.g_series()
+        mu = sgw.sgw_g0(self.ctx, G)
+        return G, mu
+
+    def polarization(self, G):
+        P0 = self.p_series()
+        sgw.sgw_polarization(self.ctx, G, P0)
+        return P0
+
+    def screened(self, P0):
+        P = self.p_series()
+        sgw.sgw_screened_interaction(self.ctx, P0, P)
+        return P
+
+    def self_energy(self, G, P):
+        Sig = self.g_series()
+        sgw.sgw_self_energy(self.ctx, G, P, Sig)
+        return Sig
+
+    def hartree_fock(self, G):
+        H = self.zeros(self.layout.g_elems)
+        sgw.sgw_hartree_fock(self.ctx, G, H)
+        return H
+
+    def dyson(self, Sig, Shf, mu, search_mu=True):
+        G = self.g_series()
+        mu = sgw.sgw_dyson(self.ctx, Sig, Shf, mu, search_mu, G)
+        return G, mu
+
+    def energy(self, G, Shf, Sig):
+        return sgw.sgw_energy(self.ctx, G, Shf, Sig)
+
+    def unfold(self, which, packed):
+        nt = packed.shape[0] if packed.dim() == 2 else 1
+        n = self.cfg.nao if which == 0 else self.cfg.naux
+        out = self.zeros(self.layout.nkpts, nt, n, n)
+        sgw.sgw_unfold(self.ctx, which, nt, packed, out)
+        self.torch.cuda.synchronize(self.device)
+        return out
+
+    def close(self):
+        if self.ctx is not None:
+            sgw.sgw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

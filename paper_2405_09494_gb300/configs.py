@@ -24,6 +24,8 @@ F50 = [-136, -69, -46, -35, -28, -24, -21, -19, -17, -16, -15, -14, -13, -12, -1
 B50 = [-196, -91, -54, -38, -30, -25, -21, -19, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7,
        -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 19, 21,
        25, 30, 38, 54, 91, 196]
+F16 = [-15, -8, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 7, 14]
+B16 = [-21, -10, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 10, 21]
 
 
 @dataclass
@@ -82,6 +84,11 @@ CONFIGS = {
         name="c2", index=1, structure="rocksalt", nk=(3, 3, 3), ao_shells=_shells({0: 1, 1: 1, 2: 1}),
         aux_shells=_shells({0: 6, 1: 5, 2: 3, 3: 2}), ntau=50, beta=100.0, mats_f=F50, mats_b=B50,
         description="rocksalt Oh, 3x3x3 mesh (4 wedge points), nao 18, naux 100, 50 tau, beta 100"),
+    # small rocksalt cell for the smoke run and the fast parity tests: 2x2x2 mesh (3 wedge points)
+    "t1": Config(
+        name="t1", index=10, structure="rocksalt", nk=(2, 2, 2), ao_shells=(0, 1), aux_shells=(0, 0, 1, 2),
+        ntau=16, beta=10.0, mats_f=F16, mats_b=B16,
+        description="rocksalt Oh, 2x2x2 mesh, nao 8, naux 20, 16 tau, beta 10"),
 }
 
 

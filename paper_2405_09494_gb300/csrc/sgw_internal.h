@@ -1,0 +1,228 @@
+// Internal declarations of the sgw library: context, device tables, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sgw.h"
+
+namespace sgw {
+
+using cplx = std::complex<double>;
+
+// Status codes written by kernels into the context's device status word.
+enum DeviceStatus : int { DEV_OK = 0, DEV_SINGULAR = 1 };
+
+// One block-diagonal partition of an index range [0, n): for every index v,
+// the first index and size of its block and the offset of the block's data
+// (row-major n_b x n_b) inside the packed matrix of that wedge point.
+struct Partition {
+  std::vector<int> sizes;      // per block
+  std::vector<int> starts;     // per index: first index of its block
+  std::vector<int> isize;      // per index: size of its block
+  std::vector<long long> doff; // per index: packed offset of its block
+  long long elems = 0;
+};
+
+// Item of a block-diagonal multiply (see bd_mult).
+struct BdItem {
+  long long x_off, y_off, m_off;
+  int part;
+  int pad;
+  double2 scale;
+};
+
+// Unit of the block-Gram kernel (see gram_*): one <= 32 x 32 tile of one
+// output block, one contiguous range of pairs.
+struct GramUnit {
+  long long a_off, b_off;  // element offsets (pair r0, first tile row) of the A and B operands
+  int rows_m, rows_n;      // tile extent
+  int r0, r1;              // pair range [r0, r1)
+};
+
+// Output tile of a Gram reduction: sums its units (in order) into the packed output.
+struct GramTile {
+  long long out_off;  // element offset of tile element (0,0) in the output
+  int ld;             // row stride of the output block
+  int rows_m, rows_n;
+  int unit_begin, unit_count;
+};
+
+// Kernel launchers (kernels.cu).
+struct BdGeom {
+  int U, Vd, Wd;        // Y[u][v][w]
+  long long xs_u, xs_v; // strides of X (w contiguous)
+  long long ys_u, ys_v;
+  int left;             // 1: partition over v (L[v][v']), 0: partition over w (R[w'][w])
+  int trans, conj;      // use M^T / conj(M)
+  int accumulate;       // Y += ...
+  int n_part;           // partition table width (Vd for left, Wd for right)
+};
+void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
+             const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st);
+
+struct GramGeom {
+  long long a_pair, b_pair;  // pair strides
+  long long a_row, b_row;    // row strides
+  long long k_outer_a, k_outer_b;  // stride of the outer K index
+  int k_inner, k_outer;      // K = k_outer * k_inner, inner contiguous
+};
+void gram_partials(const GramGeom& g, const double2* A, const double2* B, const GramUnit* units, int nunits,
+                   double2* partial, cudaStream_t st);
+void gram_reduce(const GramTile* tiles, int ntiles, const double2* partial, double2* out, double2 alpha, int accumulate,
+                 cudaStream_t st);
+
+// out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
+void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,
+                long long E, double2 alpha, int accumulate, cudaStream_t st);
+
+// Batched in-place inversion of blocks (Gauss-Jordan, partial pivoting).
+struct InvItem {
+  long long a_off;   // first source operand (P0(i Omega) block, or Sigma(i w) block)
+  long long s_off;   // S block (Dyson) / unused
+  long long f_off;   // F = H0 + Sigma_HF block (Dyson) / unused
+  long long out_off; // destination block
+  int n;
+  int m;             // frequency index (Dyson)
+  double2 weight;    // trace weight (Dyson number mode): partial = Re(weight * Tr[A^{-1} S])
+};
+enum InvMode { INV_W = 0, INV_DYSON_STORE = 1, INV_DYSON_TRACE = 2 };
+void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
+                   const double2* F, const double* nu, double mu, double2* out, double2* trace_partial,
+                   double2* scratch, int* status, cudaStream_t st);
+
+// Batched generalised Hermitian eigensolver H C = S C eps (S may be null: identity).
+struct EigItem {
+  long long h_off, s_off, c_off, e_off;
+  int n;
+  int pad;
+};
+void geneig(const EigItem* items, int nitems, int max_n, const double2* H, const double2* S, double2* C, double* eps,
+            double2* scratch, cudaStream_t st);
+
+// Deterministic sum of weighted block trace products:
+//   result = sum_items w * sum_{a,b in block} X[x_off + a n + b] * Y[y_off + b n + a]
+struct TrItem {
+  long long x_off, y_off;
+  int n;
+  int pad;
+  double2 w;
+};
+void trace_products(const TrItem* items, int nitems, const double2* X, const double2* Y, double2* partial,
+                    double2* result, cudaStream_t st);
+void sum_partials(const double2* partial, int n, double2* result, cudaStream_t st);
+
+void fill_zero(double2* p, long long n, cudaStream_t st);
+void axpby(double2* y, const double2* x, long long n, double a, double b, cudaStream_t st);  // y = a y + b x
+void max_abs_diff(const double2* a, const double2* b, long long n, unsigned long long* out_bits, cudaStream_t st);
+void pack_blocks(const double2* dense, long long dense_ld_mat, int n, const long long* blk_dense_off, const int* blk_n,
+                 const long long* blk_pack_off, int nblk, double2* packed, int to_packed, cudaStream_t st);
+void g0_closed_form(const double2* C, const double* eps, const long long* row_blk_off, const int* row_blk_n,
+                    const long long* row_e_off, long long g_elems, const double* tau, int ntau, double beta, double mu,
+                    double2* G, cudaStream_t st);
+double mu_bisect_device(const double* eps, const double* wts, int n, double beta, double n_target, double lo, double hi,
+                        double* work, cudaStream_t st);
+
+}  // namespace sgw
+
+namespace sgw {
+// Cached launch tables of one contraction (P0, Sigma or exchange), built once.
+struct ContractionPlan {
+  bool built = false;
+  int nc = 0;                         // tau values per chunk
+  long long items_per_t = 0;          // block-multiply items per tau value
+  BdItem *d_A = nullptr, *d_B = nullptr;
+  GramUnit* d_units = nullptr;
+  GramTile* d_tiles = nullptr;
+  std::vector<long long> unit_start, tile_start;  // per tau value (size nt + 1)
+  long long max_units_chunk = 0;
+  double fl_A_t = 0, fl_B_t = 0, fl_G_t = 0;  // algorithmic flops per tau value of the three stages
+};
+}  // namespace sgw
+
+// The context.  Host vectors hold the set-up tables; d_* are device copies.
+struct sgw_ctx {
+  sgw_params p{};
+  std::vector<int> mats_f, mats_b;
+  int Nk = 0, nao = 0, naux = 0, nt = 0, nwf = 0, nwb = 0;
+  std::string last_error;
+
+  // tau grid and transforms (host, row-major)
+  std::vector<double> tau;
+  std::vector<sgw::cplx> TF, TFbar, TB, TBbar;  // (nwf x nt), (nt x nwf), (nwb x nt), (nt x nwb)
+  std::vector<double> nu_f, nu_b;
+  std::vector<double> beta_row;                 // f(beta^-) = beta_row . f(tau)
+  std::vector<sgw::cplx> gamma_w;               // gamma = sum_m gamma_w[m] G(i w_m)
+  std::vector<double> gl_interp, gl_w;          // values at Gauss-Legendre nodes, weights
+  double2 *d_TF = nullptr, *d_TFbar = nullptr, *d_TB = nullptr, *d_TBbar = nullptr;
+  double2 *d_beta_row = nullptr, *d_gl_interp = nullptr;
+  double* d_nu_f = nullptr;
+  double* d_tau = nullptr;
+
+  // symmetry
+  bool built = false;
+  int nwedge = 0;
+  std::vector<int> wedge_k, rep, op, star;
+  std::vector<sgw::Partition> part_ao, part_aux;
+  std::vector<long long> g_off, p_off;
+  long long g_elems = 0, p_elems = 0;
+  int max_ao_block = 0, max_aux_block = 0;
+  double2 *d_Uao = nullptr, *d_Uaux = nullptr;  // [Nk][n][n]
+  std::vector<sgw::cplx> hostU[2];                // host copies, freed after upload
+  int *d_ao_start = nullptr, *d_ao_size = nullptr, *d_aux_start = nullptr, *d_aux_size = nullptr;
+  long long *d_ao_doff = nullptr, *d_aux_doff = nullptr;
+  int *d_full_start = nullptr, *d_full_size = nullptr;  // one block covering [0, max(nao,naux))
+  long long* d_full_doff = nullptr;
+  std::vector<int> pair_k1[2], pair_k2[2];
+
+  // inputs in block coordinates
+  double2 *d_V[2] = {nullptr, nullptr};  // [npairs][naux][nao][nao]
+  double2 *d_H0 = nullptr, *d_S = nullptr;  // packed [g_elems]
+  bool have_one_body = false, have_v[2] = {false, false};
+  std::vector<long long> v_loaded[2];
+
+  // cached launch tables
+  sgw::ContractionPlan plan_p0, plan_sigma, plan_k, plan_rho;
+  std::vector<long long> plan_k_wbeg;  // per wedge point: first unit / tile of the exchange plan
+  std::vector<long long> plan_k_tbeg;
+  // per packed orbital element: block offset, block size, eps offset, row, column, wedge point
+  long long *d_el_boff = nullptr, *d_el_eoff = nullptr;
+  int *d_el_bn = nullptr, *d_el_i = nullptr, *d_el_j = nullptr, *d_el_w = nullptr;
+  // block lists over the wedge: orbital and auxiliary
+  std::vector<long long> aob_off, auxb_off;  // packed offset
+  std::vector<int> aob_n, auxb_n, aob_w, auxb_w, aob_start, auxb_start;
+  double2* d_C0 = nullptr;   // eigenvectors of (H0, S) per block (packed)
+  double* d_eps0 = nullptr;  // eigenvalues [nwedge][nao]
+  double* d_epsw = nullptr;  // weight per eigenvalue (s / N_k * star)
+  // workspaces
+  double2* d_ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_status = nullptr;
+  double* d_scalar = nullptr;  // small host-visible results
+  unsigned long long* d_maxbits = nullptr;
+
+  // launch accounting and optional per-kernel CUDA-event timing
+  struct ProfEvent { int id; cudaEvent_t a, b; };
+  bool prof_on = false;
+  std::vector<std::string> prof_names;
+  std::vector<double> prof_ms, prof_flops;
+  std::vector<long long> prof_launch;
+  std::vector<ProfEvent> prof_pending;
+  long long launches = 0;
+
+  sgw_status fail(sgw_status s, const std::string& msg) {
+    last_error = msg;
+    return s;
+  }
+};
+
+// set-up helpers (setup.cpp)
+namespace sgw {
+sgw_status build_grid(sgw_ctx* c);
+sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st);
+sgw_status ensure_workspace(sgw_ctx* c, size_t bytes);
+}  // namespace sgw

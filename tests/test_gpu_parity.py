@@ -1,0 +1,178 @@
+"""Parity of the CUDA library (through its C ABI) with the oracle, step by step.
+
+Every library result is compared element by element with the oracle on the
+same seeded inputs.  The symmetry-adapted results are first unfolded to the
+AO basis over the whole zone (sgw_unfold), so the comparison is with the
+oracle's plain full-zone definition (the block basis is unique only up to
+unitaries inside each block).  Plain form tolerance: 1e-10 relative max-norm.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import gw
+from tests.gpu_helpers import oracle_grid, rel_err, to_np, with_grid
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _small_rocksalt(nk, ntau=16, beta=10.0):
+    from paper_2405_09494_gb300 import configs
+
+    base = configs.get("c2")
+    cfg = dataclasses.replace(base, name=f"rocksalt-{nk[0]}", nk=nk, ao_shells=(0, 1), aux_shells=(0, 0, 1, 2))
+    return with_grid(cfg, beta, ntau, "")
+
+
+def _small_diamond(nk, ntau=16, beta=10.0):
+    from paper_2405_09494_gb300 import configs
+
+    base = configs.get("c2")
+    cfg = dataclasses.replace(base, name=f"diamond-{nk[0]}", index=3, structure="diamond", nk=nk,
+                              ao_shells=(0, 1), aux_shells=(0, 0, 1, 2))
+    return with_grid(cfg, beta, ntau, "")
+
+
+class Case:
+    """Library session plus the oracle's full-zone reference chain for one workload."""
+
+    def __init__(self, cfg, search_mu_grid=False):
+        from paper_2405_09494_gb300 import api
+
+        self.cfg = cfg
+        self.sess = api.Session(cfg)
+        self.V = self.sess.sys.V_full()
+        self.og = oracle_grid(cfg)
+        s = self.sess.sys
+        self.mu0 = gw.mu_noninteracting(s.H0, s.S, cfg.beta, cfg.n_elec, cfg.spin)
+        self.G0 = gw.g0_tau(s.H0, s.S, self.mu0, cfg.beta, self.og["tau"])
+        self.P0 = gw.polarization(self.G0, self.V, cfg.nk, cfg.spin, cfg.loop_sign)
+        self.P, _, _ = gw.screened_interaction(self.P0, self.og["TB"], self.og["TBbar"])
+        self.Sig = gw.self_energy(self.G0, self.P, self.V, cfg.nk)
+        self.Shf, _, _ = gw.hartree_fock(gw.density_matrix(self.G0), self.V, cfg.nk, cfg.spin)
+        # library chain
+        self.lG0, self.lmu0 = self.sess.g0()
+        self.lP0 = self.sess.polarization(self.lG0)
+        self.lP = self.sess.screened(self.lP0)
+        self.lSig = self.sess.self_energy(self.lG0, self.lP)
+        self.lShf = self.sess.hartree_fock(self.lG0)
+
+    def unf(self, which, x):
+        out = to_np(self.sess.unfold(which, x))
+        return out if x.dim() == 2 else out[:, 0]
+
+
+@pytest.fixture(scope="module")
+def c1():
+    _need_gpu()
+    from paper_2405_09494_gb300 import configs
+
+    case = Case(configs.get("c1"))
+    yield case
+    case.sess.close()
+
+
+@pytest.fixture(scope="module")
+def c1_fine():
+    _need_gpu()
+    from paper_2405_09494_gb300 import configs
+
+    case = Case(with_grid(configs.get("c1"), 10.0, 40))
+    yield case
+    case.sess.close()
+
+
+@pytest.fixture(scope="module", params=[(2, 2, 2), (3, 3, 3)], ids=["rocksalt-2", "rocksalt-3"])
+def rocksalt(request):
+    _need_gpu()
+    case = Case(_small_rocksalt(request.param))
+    yield case
+    case.sess.close()
+
+
+@pytest.fixture(scope="module")
+def diamond():
+    _need_gpu()
+    case = Case(_small_diamond((2, 2, 2)))
+    yield case
+    case.sess.close()
+
+
+# ------------------------------------------------------------------ no symmetry (workload c1)
+def test_c1_g0_and_mu(c1):
+    assert abs(c1.lmu0 - c1.mu0) < 1e-10
+    assert rel_err(c1.unf(0, c1.lG0), c1.G0) < TOL
+
+
+def test_c1_polarization(c1):
+    assert rel_err(c1.unf(1, c1.lP0), c1.P0) < TOL
+
+
+def test_c1_screened_interaction(c1):
+    assert rel_err(c1.unf(1, c1.lP), c1.P) < TOL
+
+
+def test_c1_self_energy(c1):
+    assert rel_err(c1.unf(0, c1.lSig), c1.Sig) < TOL
+
+
+def test_c1_hartree_fock(c1):
+    assert rel_err(c1.unf(0, c1.lShf), c1.Shf) < TOL
+
+
+def test_c1_fine_dyson_mu_search_and_energy(c1_fine):
+    c = c1_fine
+    s = c.sess.sys
+    G, mu = gw.dyson(s.H0, s.S, c.Shf, c.Sig, c.mu0, c.og, c.cfg.n_elec, c.cfg.spin, search_mu=True)
+    lG, lmu = c.sess.dyson(c.lSig, c.lShf, c.lmu0, True)
+    assert abs(lmu - mu) < 1e-9
+    assert rel_err(c.unf(0, lG), G) < TOL
+    E = gw.energy(s.H0, s.S, G, c.Shf, c.Sig, c.cfg.beta, c.cfg.spin)
+    lE = c.sess.energy(lG, c.lShf, c.lSig)
+    assert abs(lE[0] - E[0].real) < 1e-10 * max(1.0, abs(E[0]))
+    assert abs(lE[3] - E[3].real) < 1e-10 * max(1.0, abs(E[0]))
+
+
+# ------------------------------------------------------------------ symmetry: unfolding identity
+def test_rocksalt_wedge_sizes(rocksalt):
+    n = rocksalt.cfg.nk[0]
+    assert rocksalt.sess.layout.nwedge == {2: 3, 3: 4}[n]
+
+
+def test_rocksalt_g0(rocksalt):
+    assert abs(rocksalt.lmu0 - rocksalt.mu0) < 1e-10
+    assert rel_err(rocksalt.unf(0, rocksalt.lG0), rocksalt.G0) < TOL
+
+
+def test_rocksalt_polarization_unfolds_to_full_zone(rocksalt):
+    assert rel_err(rocksalt.unf(1, rocksalt.lP0), rocksalt.P0) < TOL
+
+
+def test_rocksalt_screened_interaction(rocksalt):
+    assert rel_err(rocksalt.unf(1, rocksalt.lP), rocksalt.P) < TOL
+
+
+def test_rocksalt_self_energy_unfolds_to_full_zone(rocksalt):
+    assert rel_err(rocksalt.unf(0, rocksalt.lSig), rocksalt.Sig) < TOL
+
+
+def test_rocksalt_hartree_fock(rocksalt):
+    assert rel_err(rocksalt.unf(0, rocksalt.lShf), rocksalt.Shf) < TOL
+
+
+def test_diamond_nonsymmorphic_chain(diamond):
+    assert diamond.sess.layout.nwedge == 3
+    assert rel_err(diamond.unf(0, diamond.lG0), diamond.G0) < TOL
+    assert rel_err(diamond.unf(1, diamond.lP0), diamond.P0) < TOL
+    assert rel_err(diamond.unf(1, diamond.lP), diamond.P) < TOL
+    assert rel_err(diamond.unf(0, diamond.lSig), diamond.Sig) < TOL
+    assert rel_err(diamond.unf(0, diamond.lShf), diamond.Shf) < TOL

@@ -1,0 +1,101 @@
+"""Host-side set-up of the library (no GPU): transform matrices and space-group analysis.
+
+* The tau grid and the four Matsubara maps the library builds agree with the
+  oracle's independent construction.
+* The wedge sizes of the library's star analysis equal the printed n_ik column
+  of Table 2 (tests/golden/table2_wedge_sizes.json).
+* Block sizes at Gamma follow the textbook decomposition of the orbital
+  representation (e.g. O_h: s -> A1g, p -> T1u, d -> Eg + T2g) and every
+  partition covers the basis.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import grid
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _lib():
+    from paper_2405_09494_gb300 import build, sgw
+
+    if not os.path.exists(sgw.LIB_PATH):
+        try:
+            build.build()
+        except RuntimeError as e:
+            pytest.skip(str(e))
+    return sgw
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "t1"])
+def test_library_grid_matches_oracle(name):
+    sgw = _lib()
+    from paper_2405_09494_gb300 import configs
+
+    cfg = configs.get(name)
+    tau, TF, TFb, TB, TBb = sgw.sgw_host_grid(cfg.nk, cfg.nao, cfg.naux, cfg.ntau, cfg.mats_f, cfg.mats_b, cfg.beta)
+    oTF = grid.forward_map(cfg.mats_f, cfg.beta, cfg.ntau, "F")
+    oTB = grid.forward_map(cfg.mats_b, cfg.beta, cfg.ntau, "B")
+
+    def rel(a, b):
+        return np.abs(a - b).max() / np.abs(b).max()
+
+    assert np.abs(tau - grid.tau_nodes(cfg.beta, cfg.ntau)).max() < 1e-12
+    assert rel(TF, oTF) < 1e-12 and rel(TB, oTB) < 1e-12
+    assert rel(TFb, grid.backward_map(oTF)) < 1e-11 and rel(TBb, grid.backward_map(oTB)) < 1e-11
+
+
+def _groups():
+    from paper_2405_09494_gb300 import synth
+
+    oh = synth.space_group("rocksalt")
+    td = [(R, v) for R, v in oh if int(np.sum(R < 0)) % 2 == 0]
+    return {"O_h": (oh, synth.atom_positions("rocksalt")), "T_d": (td, synth.atom_positions("diamond")),
+            "Fd-3m": (synth.space_group("diamond"), synth.atom_positions("diamond"))}
+
+
+def _analyse(ops, pos, n, aos, axs):
+    sgw = _lib()
+    from paper_2405_09494_gb300 import synth
+
+    rot = np.stack([R for R, _ in ops])
+    tra = np.stack([v for _, v in ops])
+    nao = len(pos) * sum(2 * l + 1 for l in aos)
+    naux = len(pos) * sum(2 * l + 1 for l in axs)
+    return sgw.sgw_host_symmetry((n, n, n), nao, naux, synth.FCC, pos, rot, tra, aos, axs), nao, naux
+
+
+def test_wedge_sizes_match_table2():
+    gold = json.load(open(os.path.join(HERE, "golden", "table2_wedge_sizes.json")))
+    groups = _groups()
+    for gname in ("O_h", "T_d"):
+        ops, pos = groups[gname]
+        for n, expect in gold[gname].items():
+            (nw, rep, _, _), _, _ = _analyse(ops, pos, int(n), (0,), (0,))
+            assert nw == expect, (gname, n, nw)
+    # the non-symmorphic diamond group has the same point group as O_h
+    ops, pos = groups["Fd-3m"]
+    for n, expect in gold["O_h"].items():
+        (nw, _, _, _), _, _ = _analyse(ops, pos, int(n), (0,), (0,))
+        assert nw == expect
+
+
+def test_gamma_blocks_follow_the_irreducible_decomposition():
+    ops, pos = _groups()["O_h"]
+    (nw, rep, ao, ax), nao, naux = _analyse(ops, pos, 3, (0, 1, 2), (0, 1, 2, 3))
+    # O_h on two O_h sites: s -> A1g (2), p -> T1u (2 x 3), d -> Eg (2 x 2) + T2g (2 x 3)
+    assert sorted(ao[0]) == [2, 4, 6, 6]
+    # aux adds f -> A2u + T1u + T2u: T1u gathers p and f copies (12)
+    assert sorted(ax[0]) == [2, 2, 4, 6, 6, 12]
+    ops, pos = _groups()["T_d"]
+    (nw, rep, ao, ax), nao, naux = _analyse(ops, pos, 2, (0, 1, 2), (0,))
+    # T_d: s -> A1 (2), p -> T2 (2 x 3), d -> E (2 x 2) + T2 (2 x 3)
+    assert sorted(ao[0]) == [2, 4, 12]
+    for g in ("O_h", "T_d", "Fd-3m"):
+        ops, pos = _groups()[g]
+        (nw, rep, ao, ax), nao, naux = _analyse(ops, pos, 4, (0, 1, 2), (0, 1, 2, 3, 4))
+        assert all(sum(b) == nao for b in ao) and all(sum(b) == naux for b in ax)
+        assert rep.min() == 0 and rep.max() == nw - 1
