@@ -99,3 +99,24 @@ def test_gamma_blocks_follow_the_irreducible_decomposition():
         (nw, rep, ao, ax), nao, naux = _analyse(ops, pos, 4, (0, 1, 2), (0, 1, 2, 3, 4))
         assert all(sum(b) == nao for b in ao) and all(sum(b) == naux for b in ax)
         assert rep.min() == 0 and rep.max() == nw - 1
+
+
+@pytest.mark.parametrize("structure", ["rocksalt", "diamond"])
+def test_library_blocks_match_the_oracle_simultaneous_diagonalisation(structure):
+    """Irrep block sizes are unique up to order: the library's (one Hermitian combination of the
+    Dirac characters) and the oracle's (successive refinement) must agree at every wedge point."""
+    from oracle import symmetry as sy
+    from paper_2405_09494_gb300 import synth
+
+    ops = synth.space_group(structure)
+    pos = synth.atom_positions(structure)
+    aos, axs = (0, 1, 2), (0, 1, 2, 3, 4)
+    (nw, rep, ao, ax), nao, naux = _analyse(ops, pos, 4, aos, axs)
+    for shells, lib_blocks in ((aos, ao), (axs, ax)):
+        cr = sy.Crystal(synth.FCC, pos, ops, shells)
+        reps, orep = sy.stars(cr, (4, 4, 4))
+        assert len(reps) == nw and np.array_equal(orep, rep)
+        for w, k in enumerate(reps):
+            omegas, _, _ = sy.dirac_characters(cr, (4, 4, 4), k)
+            _, sizes = sy.simultaneous_diagonalize(omegas, cr.n)
+            assert sorted(sizes) == sorted(lib_blocks[w]), (structure, w, sizes, lib_blocks[w])
