@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "sgw_internal.h"
 
@@ -63,6 +64,16 @@ void free_plan(ContractionPlan& p) {
 }  // namespace
 
 namespace sgw {
+// single-precision copies of the tau series used by the chosen form (kept apart from the workspace)
+sgw_status ensure_g32(sgw_ctx* c, size_t elems) {
+  if (elems <= c->g32_elems) return SGW_OK;
+  if (c->d_g32) cudaFree(c->d_g32);
+  c->d_g32 = nullptr;
+  c->g32_elems = 0;
+  if (cudaMalloc(&c->d_g32, elems * sizeof(float2)) != cudaSuccess) return c->fail(SGW_ERR_OOM, "complex64 buffers");
+  c->g32_elems = elems;
+  return SGW_OK;
+}
 sgw_status ensure_workspace(sgw_ctx* c, size_t bytes) {
   if (bytes <= c->ws_bytes) return SGW_OK;
   if (c->d_ws) cudaFree(c->d_ws);
@@ -274,11 +285,11 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_ao_start); dfree(c->d_ao_size); dfree(c->d_ao_doff);
   dfree(c->d_aux_start); dfree(c->d_aux_size); dfree(c->d_aux_doff);
   dfree(c->d_full_start); dfree(c->d_full_size); dfree(c->d_full_doff);
-  dfree(c->d_V[0]); dfree(c->d_V[1]); dfree(c->d_H0); dfree(c->d_S);
+  dfree(c->d_V[0]); dfree(c->d_V[1]); dfree(c->d_V32[0]); dfree(c->d_V32[1]); dfree(c->d_H0); dfree(c->d_S);
   dfree(c->d_el_boff); dfree(c->d_el_eoff); dfree(c->d_el_bn); dfree(c->d_el_i); dfree(c->d_el_j); dfree(c->d_el_w);
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
-  dfree(c->d_ws); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
+  dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
   delete c;
   return SGW_OK;
 }
@@ -362,8 +373,12 @@ extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_struct
   const long long np = (long long)nw * Nk;
   for (int o = 0; o < 2; ++o) {
     dfree(c->d_V[o]);
+    dfree(c->d_V32[o]);
     if (cudaMalloc(&c->d_V[o], (size_t)np * vsize(c) * sizeof(double2)) != cudaSuccess)
       return c->fail(SGW_ERR_OOM, "allocating the interaction tensor");
+    if (c->p.precision == SGW_MIXED_FP32 &&
+        cudaMalloc(&c->d_V32[o], (size_t)np * vsize(c) * sizeof(float2)) != cudaSuccess)
+      return c->fail(SGW_ERR_OOM, "allocating the single-precision interaction tensor");
     c->have_v[o] = false;
     c->v_loaded[o].assign(np, 0);
   }
@@ -537,6 +552,10 @@ extern "C" SGW_API sgw_status sgw_load_v(sgw_ctx* c, int which, long long first,
       bd_mult(geom(naux, nao, nao, 0, 0, 0, 0, W), Z, c->d_V[which], c->d_Uao, d_items + 2 * np_, np_,
               c->d_full_start, c->d_full_size, c->d_full_doff, st);
     });
+    if (c->p.precision == SGW_MIXED_FP32) {
+      const long long pbeg = first + p0;
+      run(c, "convert", 0.0, 1, st, [&] { to_c64(c->d_V[which] + pbeg * vs, c->d_V32[which] + pbeg * vs, np_ * vs, st); });
+    }
     CK(cudaStreamSynchronize(st));
     for (long long i = 0; i < np_; ++i) c->v_loaded[which][first + p0 + i] = 1;
   }
@@ -667,22 +686,17 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
   return SGW_OK;
 }
 
-extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, void* P0_tau, sgw_stream stream) {
-  CKS(need_built(c));
-  if (!c->have_v[0]) return c->fail(SGW_ERR_STATE, "polarization pairs of V not loaded");
-  if (!G_tau || !P0_tau) return SGW_ERR_ARG;
-  CKS(build_p0_plan(c));
+template <typename Z>
+static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2* out, cudaStream_t st, const char* tag) {
   ContractionPlan& P = c->plan_p0;
-  cudaStream_t st = S(stream);
   const int nt = c->nt, nao = c->nao, naux = c->naux, nc = P.nc;
   const long long vs = vsize(c), np = P.items_per_t;
   const size_t inter = (size_t)np * nc * vs;
-  CKS(ensure_workspace(c, (2 * inter + (size_t)P.max_units_chunk * 1024) * sizeof(double2)));
-  double2* Z = c->d_ws;
-  double2* X = Z + inter;
-  double2* part = X + inter;
-  const double2* G = static_cast<const double2*>(G_tau);
-  double2* out = static_cast<double2*>(P0_tau);
+  const size_t gsz = std::is_same<Z, float2>::value ? (size_t)nt * c->g_elems : 0;
+  CKS(ensure_workspace(c, (2 * inter + (size_t)P.max_units_chunk * 1024 + gsz) * sizeof(Z)));
+  Z* Zw = reinterpret_cast<Z*>(c->d_ws);
+  Z* X = Zw + inter;
+  Z* part = X + inter;
   GramGeom gg;
   gg.a_pair = (long long)nc * vs;
   gg.b_pair = vs;
@@ -693,24 +707,44 @@ extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, vo
   gg.k_inner = nao * nao;
   gg.k_outer = 1;
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
+  const std::string t_vg = std::string("p0_vg") + tag, t_gvg = std::string("p0_gvg") + tag,
+                    t_gram = std::string("p0_gram") + tag;
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc);
     const long long ni = (long long)(t1 - t0) * np;
-    // Z[A][c][j] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
     const int ntc = t1 - t0;
-    run(c, "p0_vg", P.fl_A_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), c->d_V[0], Z, G, P.d_A + (size_t)t0 * np, ni,
-              c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+    // Z[A][c][j] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
+    run(c, t_vg.c_str(), P.fl_A_t * ntc, 1, st, [&] {
+      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, Zw, G, P.d_A + (size_t)t0 * np, ni, c->d_ao_start,
+              c->d_ao_size, c->d_ao_doff, st);
     });
     // X[A][i][j] = sum_c G^k(-tau)[i][c] Z[A][c][j]
-    run(c, "p0_gvg", P.fl_B_t * ntc, 1, st, [&] {
-      bd_mult(geom(naux, nao, nao, 1, 0, 0, 0, nao), Z, X, G, P.d_B + (size_t)t0 * np, ni, c->d_ao_start,
+    run(c, t_gvg.c_str(), P.fl_B_t * ntc, 1, st, [&] {
+      bd_mult(geom(naux, nao, nao, 1, 0, 0, 0, nao), Zw, X, G, P.d_B + (size_t)t0 * np, ni, c->d_ao_start,
               c->d_ao_size, c->d_ao_doff, st);
     });
     const long long u0 = P.unit_start[t0], u1 = P.unit_start[t1];
     const long long ti0 = P.tile_start[t0], ti1 = P.tile_start[t1];
-    run(c, "p0_gram", P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X, c->d_V[0], P.d_units + u0, (int)(u1 - u0), part, st); });
+    run(c, t_gram.c_str(), P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X, V, P.d_units + u0, (int)(u1 - u0), part, st); });
     run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(alpha), 0, st); });
+  }
+  return SGW_OK;
+}
+
+extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, void* P0_tau, sgw_stream stream) {
+  CKS(need_built(c));
+  if (!c->have_v[0]) return c->fail(SGW_ERR_STATE, "polarization pairs of V not loaded");
+  if (!G_tau || !P0_tau) return SGW_ERR_ARG;
+  CKS(build_p0_plan(c));
+  cudaStream_t st = S(stream);
+  double2* out = static_cast<double2*>(P0_tau);
+  if (c->p.precision == SGW_MIXED_FP32) {
+    // G(tau) rounded to complex64 once; the chains accumulate in FP32, P0 is returned in FP64
+    CKS(ensure_g32(c, (size_t)c->nt * c->g_elems));
+    run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)c->nt * c->g_elems, st); });
+    CKS(polarization_impl<float2>(c, c->d_g32, c->d_V32[0], out, st, "_f32"));
+  } else {
+    CKS(polarization_impl<double2>(c, static_cast<const double2*>(G_tau), c->d_V[0], out, st, ""));
   }
   CK(cudaGetLastError());
   return SGW_OK;
@@ -849,21 +883,17 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
   return SGW_OK;
 }
 
-extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau,
-                                              sgw_stream stream) {
-  CKS(need_built(c));
-  if (!c->have_v[1]) return c->fail(SGW_ERR_STATE, "self-energy pairs of V not loaded");
-  if (!G_tau || !P_tau || !Sigma_tau) return SGW_ERR_ARG;
-  CKS(build_sigma_plan(c));
+template <typename Z>
+static sgw_status self_energy_impl(sgw_ctx* c, const Z* G, const Z* Pt, const Z* V, double2* out, cudaStream_t st,
+                                   const char* tag) {
   ContractionPlan& P = c->plan_sigma;
-  cudaStream_t st = S(stream);
   const int nt = c->nt, nao = c->nao, naux = c->naux, nc = P.nc;
   const long long vs = vsize(c), np = P.items_per_t;
   const size_t inter = (size_t)np * nc * vs;
-  CKS(ensure_workspace(c, (2 * inter + (size_t)P.max_units_chunk * 1024) * sizeof(double2)));
-  double2* X1 = c->d_ws;
-  double2* X2 = X1 + inter;
-  double2* part = X2 + inter;
+  CKS(ensure_workspace(c, (2 * inter + (size_t)P.max_units_chunk * 1024) * sizeof(Z)));
+  Z* X1 = reinterpret_cast<Z*>(c->d_ws);
+  Z* X2 = X1 + inter;
+  Z* part = X2 + inter;
   GramGeom gg;
   gg.a_pair = (long long)nc * vs;
   gg.b_pair = vs;
@@ -873,26 +903,49 @@ extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, con
   gg.k_outer_b = (long long)nao * nao;
   gg.k_inner = nao;
   gg.k_outer = naux;
+  const std::string t_vg = std::string("sigma_vg") + tag, t_pvg = std::string("sigma_pvg") + tag,
+                    t_gram = std::string("sigma_gram") + tag;
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc);
     const long long ni = (long long)(t1 - t0) * np;
-    // X1[A][i][b] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
     const int ntc = t1 - t0;
-    run(c, "sigma_vg", P.fl_A_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), c->d_V[1], X1, static_cast<const double2*>(G_tau),
-              P.d_A + (size_t)t0 * np, ni, c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+    // X1[A][i][b] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
+    run(c, t_vg.c_str(), P.fl_A_t * ntc, 1, st, [&] {
+      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, X1, G, P.d_A + (size_t)t0 * np, ni, c->d_ao_start,
+              c->d_ao_size, c->d_ao_doff, st);
     });
     // X2[A'][(i,b)] = sum_A P^q(tau)[A][A'] X1[A][(i,b)]
-    run(c, "sigma_pvg", P.fl_B_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux, nao * nao, 1, 1, 0, 0, naux), X1, X2, static_cast<const double2*>(P_tau),
-              P.d_B + (size_t)t0 * np, ni, c->d_aux_start, c->d_aux_size, c->d_aux_doff, st);
+    run(c, t_pvg.c_str(), P.fl_B_t * ntc, 1, st, [&] {
+      bd_mult(geom(1, naux, nao * nao, 1, 1, 0, 0, naux), X1, X2, Pt, P.d_B + (size_t)t0 * np, ni, c->d_aux_start,
+              c->d_aux_size, c->d_aux_doff, st);
     });
     const long long u0 = P.unit_start[t0], u1 = P.unit_start[t1];
     const long long ti0 = P.tile_start[t0], ti1 = P.tile_start[t1];
-    run(c, "sigma_gram", P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X2, c->d_V[1], P.d_units + u0, (int)(u1 - u0), part, st); });
+    run(c, t_gram.c_str(), P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X2, V, P.d_units + u0, (int)(u1 - u0), part, st); });
     run(c, "gram_reduce", 0.0, 1, st, [&] {
-      gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, static_cast<double2*>(Sigma_tau), z(-1.0 / c->Nk), 0, st);
+      gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(-1.0 / c->Nk), 0, st);
     });
+  }
+  return SGW_OK;
+}
+
+extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau,
+                                              sgw_stream stream) {
+  CKS(need_built(c));
+  if (!c->have_v[1]) return c->fail(SGW_ERR_STATE, "self-energy pairs of V not loaded");
+  if (!G_tau || !P_tau || !Sigma_tau) return SGW_ERR_ARG;
+  CKS(build_sigma_plan(c));
+  cudaStream_t st = S(stream);
+  double2* out = static_cast<double2*>(Sigma_tau);
+  if (c->p.precision == SGW_MIXED_FP32) {
+    const size_t gn = (size_t)c->nt * c->g_elems, pn = (size_t)c->nt * c->p_elems;
+    CKS(ensure_g32(c, gn + pn));
+    run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)gn, st); });
+    run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(P_tau), c->d_g32 + gn, (long long)pn, st); });
+    CKS(self_energy_impl<float2>(c, c->d_g32, c->d_g32 + gn, c->d_V32[1], out, st, "_f32"));
+  } else {
+    CKS(self_energy_impl<double2>(c, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau), c->d_V[1],
+                                  out, st, ""));
   }
   CK(cudaGetLastError());
   return SGW_OK;

@@ -35,6 +35,31 @@ __device__ __forceinline__ double2 cfma_cj(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// single-precision counterparts (chosen form: FP32 operands, FP32 accumulation)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 cfma_cj(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(a.y, b.y, c.x);
+  c.y = fmaf(a.y, b.x, c.y);
+  c.y = fmaf(-a.x, b.y, c.y);
+  return c;
+}
+template <typename Z> __device__ __forceinline__ Z czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 to_z(double2 a, double2) { return a; }
+__device__ __forceinline__ float2 to_z(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
+
 static inline unsigned grid_for(long long work, int threads, long long cap = 1 << 20) {
   long long b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -50,8 +75,9 @@ static inline unsigned grid_for(long long work, int threads, long long cap = 1 <
 // trans/conj select M^T / conj(M).  One thread per output element, looping
 // over exactly the elements of its block: no padding work for uneven blocks.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const double2* __restrict__ X, double2* __restrict__ Y,
-                                                 const double2* __restrict__ M, const BdItem* __restrict__ items,
+template <typename Z>
+__global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__ X, Z* __restrict__ Y,
+                                                 const Z* __restrict__ M, const BdItem* __restrict__ items,
                                                  long long nitems, const int* __restrict__ ps,
                                                  const int* __restrict__ pz, const long long* __restrict__ pd) {
   const int VW = g.Vd * g.Wd;
@@ -66,38 +92,39 @@ __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const double2* __rest
       const int r = e - u * VW;
       const int v = r / g.Wd;
       const int w = r - v * g.Wd;
-      double2 acc = make_double2(0.0, 0.0);
+      Z acc = czero<Z>();
       if (g.left) {
         const int st = bs[v], n = bz[v];
-        const double2* Mb = M + item.m_off + bd[v];
+        const Z* Mb = M + item.m_off + bd[v];
         const int lv = v - st;
-        const double2* Xp = X + item.x_off + (long long)u * g.xs_u + w + (long long)st * g.xs_v;
+        const Z* Xp = X + item.x_off + (long long)u * g.xs_u + w + (long long)st * g.xs_v;
         for (int j = 0; j < n; ++j) {
-          double2 m = g.trans ? Mb[(long long)j * n + lv] : Mb[(long long)lv * n + j];
+          Z m = g.trans ? Mb[(long long)j * n + lv] : Mb[(long long)lv * n + j];
           if (g.conj) m.y = -m.y;
           acc = cfma(m, Xp[(long long)j * g.xs_v], acc);
         }
       } else {
         const int st = bs[w], n = bz[w];
-        const double2* Mb = M + item.m_off + bd[w];
+        const Z* Mb = M + item.m_off + bd[w];
         const int lw = w - st;
-        const double2* Xp = X + item.x_off + (long long)u * g.xs_u + (long long)v * g.xs_v + st;
+        const Z* Xp = X + item.x_off + (long long)u * g.xs_u + (long long)v * g.xs_v + st;
         for (int j = 0; j < n; ++j) {
-          double2 m = g.trans ? Mb[(long long)lw * n + j] : Mb[(long long)j * n + lw];
+          Z m = g.trans ? Mb[(long long)lw * n + j] : Mb[(long long)j * n + lw];
           if (g.conj) m.y = -m.y;
           acc = cfma(Xp[j], m, acc);
         }
       }
-      acc = cmul(item.scale, acc);
-      double2* yp = Y + item.y_off + (long long)u * g.ys_u + (long long)v * g.ys_v + w;
+      acc = cmul(to_z(item.scale, acc), acc);
+      Z* yp = Y + item.y_off + (long long)u * g.ys_u + (long long)v * g.ys_v + w;
       if (g.accumulate) acc = cadd(*yp, acc);
       *yp = acc;
     }
   }
 }
 
-void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
-             const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st) {
+template <typename Z>
+static void bd_mult_t(const BdGeom& g, const Z* X, Z* Y, const Z* M, const BdItem* items, long long nitems,
+                      const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st) {
   if (nitems <= 0) return;
   const long long E = (long long)g.U * g.Vd * g.Wd;
   unsigned bx = grid_for(E, 256, 4096);
@@ -106,7 +133,15 @@ void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, co
   if (want < by) by = want;
   if (by > nitems) by = nitems;
   if (by < 1) by = 1;
-  k_bd_mult<<<dim3(bx, (unsigned)by), 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff);
+  k_bd_mult<Z><<<dim3(bx, (unsigned)by), 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff);
+}
+void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
+             const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st) {
+  bd_mult_t<double2>(g, X, Y, M, items, nitems, p_start, p_size, p_doff, st);
+}
+void bd_mult(const BdGeom& g, const float2* X, float2* Y, const float2* M, const BdItem* items, long long nitems,
+             const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st) {
+  bd_mult_t<float2>(g, X, Y, M, items, nitems, p_start, p_size, p_doff, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,13 +158,14 @@ __device__ __forceinline__ int gram_chunk(int rows) {
   return rows <= 1 ? 512 : rows <= 2 ? 256 : rows <= 4 ? 128 : rows <= 8 ? 64 : rows <= 16 ? 32 : 16;
 }
 
-__global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const double2* __restrict__ A,
-                                                       const double2* __restrict__ B,
+template <typename Z>
+__global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __restrict__ A,
+                                                       const Z* __restrict__ B,
                                                        const GramUnit* __restrict__ units,
-                                                       double2* __restrict__ partial) {
-  __shared__ double2 As[kGramSlots];
-  __shared__ double2 Bs[kGramSlots];
-  __shared__ double2 red[256];
+                                                       Z* __restrict__ partial) {
+  __shared__ Z As[kGramSlots];
+  __shared__ Z Bs[kGramSlots];
+  __shared__ Z red[256];
   const GramUnit u = units[blockIdx.x];
   const int tid = threadIdx.x;
   const int rmax = u.rows_m > u.rows_n ? u.rows_m : u.rows_n;
@@ -142,17 +178,17 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const double2
   const int en = big ? 0 : (tid % mn) % u.rows_n;
   const int kp = big ? 0 : tid / mn;
   const int ty = tid >> 4, tx = tid & 15;
-  double2 acc0 = make_double2(0, 0), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+  Z acc0 = czero<Z>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
   const int K = g.k_inner * g.k_outer;
   const int nload = rmax * KC;
   for (int r = u.r0; r < u.r1; ++r) {
-    const double2* Ap = A + u.a_off + (long long)(r - u.r0) * g.a_pair;
-    const double2* Bp = B + u.b_off + (long long)(r - u.r0) * g.b_pair;
+    const Z* Ap = A + u.a_off + (long long)(r - u.r0) * g.a_pair;
+    const Z* Bp = B + u.b_off + (long long)(r - u.r0) * g.b_pair;
     for (int k0 = 0; k0 < K; k0 += KC) {
       for (int idx = tid; idx < nload; idx += 256) {
         const int i = idx / KC, kk = idx - i * KC;
         const int k = k0 + kk;
-        double2 va = make_double2(0, 0), vb = va;
+        Z va = czero<Z>(), vb = va;
         if (k < K) {
           const int ko = k / g.k_inner, ki = k - ko * g.k_inner;
           if (i < u.rows_m) va = Ap[(long long)i * g.a_row + (long long)ko * g.k_outer_a + ki];
@@ -166,8 +202,8 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const double2
         // 2x2 micro tile: rows ty, ty+16; columns tx, tx+16
 #pragma unroll 4
         for (int kk = 0; kk < KC; ++kk) {
-          const double2 a0 = As[ty * LD + kk], a1 = As[(ty + 16) * LD + kk];
-          const double2 b0 = Bs[tx * LD + kk], b1 = Bs[(tx + 16) * LD + kk];
+          const Z a0 = As[ty * LD + kk], a1 = As[(ty + 16) * LD + kk];
+          const Z b0 = Bs[tx * LD + kk], b1 = Bs[(tx + 16) * LD + kk];
           acc0 = cfma_cj(a0, b0, acc0);
           acc1 = cfma_cj(a0, b1, acc1);
           acc2 = cfma_cj(a1, b0, acc2);
@@ -179,7 +215,7 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const double2
       __syncthreads();
     }
   }
-  double2* out = partial + (long long)blockIdx.x * 1024;
+  Z* out = partial + (long long)blockIdx.x * 1024;
   if (big) {
     if (ty < u.rows_m && tx < u.rows_n) out[ty * 32 + tx] = acc0;
     if (ty < u.rows_m && tx + 16 < u.rows_n) out[ty * 32 + tx + 16] = acc1;
@@ -189,21 +225,26 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const double2
     red[tid] = acc0;
     __syncthreads();
     if (tid < mn) {
-      double2 s = make_double2(0, 0);
+      Z s = czero<Z>();
       for (int p = 0; p < P; ++p) s = cadd(s, red[p * mn + tid]);
       out[em * 32 + en] = s;
     }
   }
 }
 
+template <typename Z>
 __global__ void __launch_bounds__(256) k_gram_reduce(const GramTile* __restrict__ tiles,
-                                                     const double2* __restrict__ partial, double2* __restrict__ out,
+                                                     const Z* __restrict__ partial, double2* __restrict__ out,
                                                      double2 alpha, int accumulate) {
   const GramTile t = tiles[blockIdx.x];
   for (int e = threadIdx.x; e < t.rows_m * t.rows_n; e += blockDim.x) {
     const int i = e / t.rows_n, j = e - i * t.rows_n;
     double2 s = make_double2(0, 0);
-    for (int q = 0; q < t.unit_count; ++q) s = cadd(s, partial[(long long)(t.unit_begin + q) * 1024 + i * 32 + j]);
+    for (int q = 0; q < t.unit_count; ++q) {
+      const Z p = partial[(long long)(t.unit_begin + q) * 1024 + i * 32 + j];
+      s.x += (double)p.x;
+      s.y += (double)p.y;
+    }
     s = cmul(alpha, s);
     double2* o = out + t.out_off + (long long)i * t.ld + j;
     if (accumulate) s = cadd(*o, s);
@@ -214,13 +255,32 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const GramTile* __restrict_
 void gram_partials(const GramGeom& g, const double2* A, const double2* B, const GramUnit* units, int nunits,
                    double2* partial, cudaStream_t st) {
   if (nunits <= 0) return;
-  k_gram_partials<<<nunits, 256, 0, st>>>(g, A, B, units, partial);
+  k_gram_partials<double2><<<nunits, 256, 0, st>>>(g, A, B, units, partial);
+}
+void gram_partials(const GramGeom& g, const float2* A, const float2* B, const GramUnit* units, int nunits,
+                   float2* partial, cudaStream_t st) {
+  if (nunits <= 0) return;
+  k_gram_partials<float2><<<nunits, 256, 0, st>>>(g, A, B, units, partial);
 }
 
 void gram_reduce(const GramTile* tiles, int ntiles, const double2* partial, double2* out, double2 alpha, int accumulate,
                  cudaStream_t st) {
   if (ntiles <= 0) return;
-  k_gram_reduce<<<ntiles, 256, 0, st>>>(tiles, partial, out, alpha, accumulate);
+  k_gram_reduce<double2><<<ntiles, 256, 0, st>>>(tiles, partial, out, alpha, accumulate);
+}
+void gram_reduce(const GramTile* tiles, int ntiles, const float2* partial, double2* out, double2 alpha, int accumulate,
+                 cudaStream_t st) {
+  if (ntiles <= 0) return;
+  k_gram_reduce<float2><<<ntiles, 256, 0, st>>>(tiles, partial, out, alpha, accumulate);
+}
+
+// precision conversion of packed families
+__global__ void k_to_c64(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+void to_c64(const double2* a, float2* b, long long n, cudaStream_t st) {
+  if (n > 0) k_to_c64<<<grid_for(n, 256, 8192), 256, 0, st>>>(a, b, n);
 }
 
 // ---------------------------------------------------------------------------

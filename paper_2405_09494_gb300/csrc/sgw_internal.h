@@ -64,6 +64,8 @@ struct BdGeom {
 };
 void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
              const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st);
+void bd_mult(const BdGeom& g, const float2* X, float2* Y, const float2* M, const BdItem* items, long long nitems,
+             const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st);
 
 struct GramGeom {
   long long a_pair, b_pair;  // pair strides
@@ -75,6 +77,11 @@ void gram_partials(const GramGeom& g, const double2* A, const double2* B, const 
                    double2* partial, cudaStream_t st);
 void gram_reduce(const GramTile* tiles, int ntiles, const double2* partial, double2* out, double2 alpha, int accumulate,
                  cudaStream_t st);
+void gram_partials(const GramGeom& g, const float2* A, const float2* B, const GramUnit* units, int nunits,
+                   float2* partial, cudaStream_t st);
+void gram_reduce(const GramTile* tiles, int ntiles, const float2* partial, double2* out, double2 alpha, int accumulate,
+                 cudaStream_t st);
+void to_c64(const double2* a, float2* b, long long n, cudaStream_t st);
 
 // out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
 void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,
@@ -181,6 +188,9 @@ struct sgw_ctx {
 
   // inputs in block coordinates
   double2 *d_V[2] = {nullptr, nullptr};  // [npairs][naux][nao][nao]
+  float2* d_V32[2] = {nullptr, nullptr};  // complex64 copies for the chosen form
+  float2* d_g32 = nullptr;                 // complex64 tau series (chosen form)
+  size_t g32_elems = 0;
   double2 *d_H0 = nullptr, *d_S = nullptr;  // packed [g_elems]
   bool have_one_body = false, have_v[2] = {false, false};
   std::vector<long long> v_loaded[2];
@@ -225,4 +235,5 @@ namespace sgw {
 sgw_status build_grid(sgw_ctx* c);
 sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st);
 sgw_status ensure_workspace(sgw_ctx* c, size_t bytes);
+sgw_status ensure_g32(sgw_ctx* c, size_t elems);
 }  // namespace sgw

@@ -1,0 +1,65 @@
+"""Chosen form (mixed precision) against the oracle, error stated per quantity.
+
+The V-G-V and V-G-P-V chains run with complex64 operands and FP32
+accumulation; the W solve, Dyson, mu search and transforms stay FP64.  The
+gate is 1e-5 relative max-norm on P0, P, Sigma~ and the energy (the bound the
+chosen form is held to); the measured errors are printed.
+"""
+import numpy as np
+import pytest
+
+from oracle import gw
+from tests.gpu_helpers import oracle_grid, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mixed_t1():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_09494_gb300 import api, configs, sgw
+
+    cfg = configs.get("t1")
+    sess = api.Session(cfg, precision=sgw.SGW_MIXED_FP32)
+    s = sess.sys
+    V = s.V_full()
+    og = oracle_grid(cfg)
+    mu0 = gw.mu_noninteracting(s.H0, s.S, cfg.beta, cfg.n_elec)
+    G0 = gw.g0_tau(s.H0, s.S, mu0, cfg.beta, og["tau"])
+    P0 = gw.polarization(G0, V, cfg.nk)
+    P, _, _ = gw.screened_interaction(P0, og["TB"], og["TBbar"])
+    Sig = gw.self_energy(G0, P, V, cfg.nk)
+    Shf, _, _ = gw.hartree_fock(gw.density_matrix(G0), V, cfg.nk)
+    G1, mu1 = gw.dyson(s.H0, s.S, Shf, Sig, mu0, og, cfg.n_elec, search_mu=True)
+    E = gw.energy(s.H0, s.S, G1, Shf, Sig, cfg.beta)
+    lG0, lmu0 = sess.g0()
+    lP0 = sess.polarization(lG0)
+    lP = sess.screened(lP0)
+    lSig = sess.self_energy(lG0, lP)
+    lShf = sess.hartree_fock(lG0)
+    lG1, lmu1 = sess.dyson(lSig, lShf, lmu0, True)
+    lE = sess.energy(lG1, lShf, lSig)
+    out = dict(
+        P0=rel_err(to_np(sess.unfold(1, lP0)), P0),
+        P=rel_err(to_np(sess.unfold(1, lP)), P),
+        Sigma=rel_err(to_np(sess.unfold(0, lSig)), Sig),
+        G=rel_err(to_np(sess.unfold(0, lG1)), G1),
+        mu=abs(lmu1 - mu1),
+        E=abs(lE[0] - E[0].real) / max(1.0, abs(E[0])),
+    )
+    print("chosen-form errors vs the FP64 oracle:", {k: f"{v:.2e}" for k, v in out.items()})
+    sess.close()
+    return out
+
+
+@pytest.mark.parametrize("q", ["P0", "P", "Sigma", "G", "E"])
+def test_mixed_form_error_per_quantity(mixed_t1, q):
+    assert mixed_t1[q] < TOL, (q, mixed_t1[q])
+
+
+def test_mixed_form_is_not_the_plain_form(mixed_t1):
+    # the FP32 chains leave a visible rounding signature: not bitwise the FP64 result
+    assert mixed_t1["P0"] > 1e-12
