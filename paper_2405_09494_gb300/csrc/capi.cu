@@ -72,6 +72,7 @@ sgw_status ensure_g32(sgw_ctx* c, size_t elems) {
   c->g32_elems = 0;
   if (cudaMalloc(&c->d_g32, elems * sizeof(float2)) != cudaSuccess) return c->fail(SGW_ERR_OOM, "complex64 buffers");
   c->g32_elems = elems;
+  ++c->ws_gen;  // a captured iteration that used the old buffer must be re-captured
   return SGW_OK;
 }
 sgw_status ensure_workspace(sgw_ctx* c, size_t bytes) {
@@ -81,6 +82,7 @@ sgw_status ensure_workspace(sgw_ctx* c, size_t bytes) {
   c->ws_bytes = 0;
   if (cudaMalloc(&c->d_ws, bytes) != cudaSuccess) return c->fail(SGW_ERR_OOM, "workspace allocation failed");
   c->ws_bytes = bytes;
+  ++c->ws_gen;
   return SGW_OK;
 }
 }  // namespace sgw
@@ -167,13 +169,19 @@ static BdGeom geom(int U, int Vd, int Wd, int left, int trans, int conj, int acc
 // A rows start at a_off (+ row * a_row), B rows at b_off; pairs [0, npair) with strides.
 static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& tiles, long long unit_base, int nb,
                            long long out_off, long long a_off, long long b_off, long long a_row, long long b_row,
-                           int npair, long long kwork) {
-  for (int tm = 0; tm < nb; tm += 32)
-    for (int tn = 0; tn < nb; tn += 32) {
-      const int rm = std::min(32, nb - tm), rn = std::min(32, nb - tn);
+                           int npair, long long kwork, long long target = (1LL << 20)) {
+  // balanced square tiles of at most 32 rows
+  const int nt_side = (nb + 31) / 32;
+  const int ts = (nb + nt_side - 1) / nt_side;
+  for (int tm = 0; tm < nb; tm += ts)
+    for (int tn = 0; tn < nb; tn += ts) {
+      const int rm = std::min(ts, nb - tm), rn = std::min(ts, nb - tn);
       long long per_pair = (long long)rm * rn * kwork;
-      long long chunk = std::max(1LL, (1LL << 20) / std::max(1LL, per_pair));
+      long long chunk = std::max(1LL, target / std::max(1LL, per_pair));
       if (chunk > npair) chunk = npair;
+      // spread the pairs evenly over the units of this tile
+      const long long nun = (npair + chunk - 1) / chunk;
+      chunk = (npair + nun - 1) / nun;
       GramTile t;
       t.out_off = out_off + (long long)tm * nb + tn;
       t.ld = nb;
@@ -189,6 +197,8 @@ static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& 
         u.r1 = (int)std::min<long long>(npair, r0 + chunk);
         u.a_off = a_off + (long long)tm * a_row;
         u.b_off = b_off + (long long)tn * b_row;
+        u.slot = (int)((long long)units.size() - unit_base);
+        u.pad = 0;
         units.push_back(u);
         ++cnt;
       }
@@ -203,6 +213,20 @@ static void finalize_units(std::vector<GramUnit>& units, size_t from, long long 
     units[i].a_off += (long long)units[i].r0 * a_pair;
     units[i].b_off += (long long)units[i].r0 * b_pair;
   }
+}
+
+// Order the units of one launch [from, end) largest first (their slots keep the tiles' addressing).
+static void schedule_units(std::vector<GramUnit>& units, size_t from, long long kwork) {
+  std::stable_sort(units.begin() + from, units.end(), [&](const GramUnit& a, const GramUnit& b) {
+    return (long long)a.rows_m * a.rows_n * (a.r1 - a.r0) > (long long)b.rows_m * b.rows_n * (b.r1 - b.r0);
+  });
+  (void)kwork;
+}
+
+// Target multiply-adds per unit so that a launch of `work` fills the GPU several times over.
+static long long unit_target(double work) {
+  const double t = work / (152.0 * 8.0);
+  return std::max(1LL << 14, std::min(1LL << 22, (long long)t));
 }
 
 // ---------------------------------------------------------------------------
@@ -267,7 +291,7 @@ extern "C" SGW_API sgw_status sgw_create(const sgw_params* p, sgw_ctx** out) {
     return s;
   }
   if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_scalar, 64 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->d_maxbits, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->d_maxbits, 2 * sizeof(unsigned long long)) != cudaSuccess) {
     sgw_destroy(c);
     return SGW_ERR_OOM;
   }
@@ -290,6 +314,11 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
+  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
+  dfree(c->d_it_P0); dfree(c->d_it_P); dfree(c->d_it_S); dfree(c->d_it_H);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->it_exec) cudaGraphExecDestroy(c->it_exec);
+  if (c->it_graph) cudaGraphDestroy(c->it_graph);
   delete c;
   return SGW_OK;
 }
@@ -650,8 +679,14 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
   P.unit_start.assign(nt + 1, 0);
   P.tile_start.assign(nt + 1, 0);
   long long base = 0;
+  double work_t = 0;
+  for (size_t b = 0; b < c->auxb_off.size(); ++b) work_t += (double)c->auxb_n[b] * c->auxb_n[b] * nao * nao * Nk;
+  const long long target = unit_target(work_t * nc);
   for (int t = 0; t < nt; ++t) {
-    if (t % nc == 0) base = (long long)units.size();
+    if (t % nc == 0) {
+      if (t > 0) schedule_units(units, (size_t)base, 0);
+      base = (long long)units.size();
+    }
     P.unit_start[t] = units.size();
     P.tile_start[t] = tiles.size();
     const int tl = t % nc;
@@ -661,10 +696,11 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->p_elems + c->auxb_off[b],
                      (p0 * nc + tl) * vs + (long long)st * nao * nao, p0 * vs + (long long)st * nao * nao,
-                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao);
+                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
+  schedule_units(units, (size_t)base, 0);
   P.unit_start[nt] = units.size();
   P.tile_start[nt] = tiles.size();
   P.max_units_chunk = 0;
@@ -751,49 +787,86 @@ extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, vo
 }
 
 // ---------------------------------------------------------------------------
-// a4-a6: screened interaction
+// static launch tables of the hot path
 // ---------------------------------------------------------------------------
-extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P0_tau, void* P_tau, sgw_stream stream) {
-  CKS(need_built(c));
-  if (!P0_tau || !P_tau) return SGW_ERR_ARG;
-  cudaStream_t st = S(stream);
-  const long long pe = c->p_elems;
-  std::vector<InvItem> items;
+static sgw_status ensure_tables(sgw_ctx* c) {
+  if (c->tables) return SGW_OK;
+  std::vector<InvItem> w;
   for (int m = 0; m < c->nwb; ++m)
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
       InvItem it;
-      it.a_off = (long long)m * pe + c->auxb_off[b];
+      it.a_off = (long long)m * c->p_elems + c->auxb_off[b];
       it.s_off = it.f_off = 0;
       it.out_off = it.a_off;
       it.n = c->auxb_n[b];
       it.m = m;
       it.weight = z(0.0);
-      items.push_back(it);
+      w.push_back(it);
     }
+  std::vector<InvItem> d;
+  for (int m = 0; m < c->nwf; ++m)
+    for (size_t b = 0; b < c->aob_off.size(); ++b) {
+      InvItem it;
+      it.a_off = (long long)m * c->g_elems + c->aob_off[b];
+      it.s_off = c->aob_off[b];
+      it.f_off = c->aob_off[b];
+      it.out_off = it.a_off;
+      it.n = c->aob_n[b];
+      it.m = m;
+      const double wk = (double)c->p.spin_factor / c->Nk * c->star[c->aob_w[b]];
+      it.weight = z(wk * c->gamma_w[m].real(), wk * c->gamma_w[m].imag());
+      d.push_back(it);
+    }
+  const size_t nb = c->aob_off.size();
+  const long long mat = (long long)c->nao * c->nao, vs = vsize(c);
+  std::vector<long long> tab(3 * nb + c->nwedge);
+  for (size_t b = 0; b < nb; ++b) {
+    tab[b] = c->aob_w[b] * mat + (long long)c->aob_start[b] * c->nao + c->aob_start[b];
+    tab[nb + b] = c->aob_off[b];
+  }
+  int* bn = reinterpret_cast<int*>(tab.data() + 2 * nb);
+  for (size_t b = 0; b < nb; ++b) bn[b] = c->aob_n[b];
+  const int wG = c->rep[0];
+  for (int w = 0; w < c->nwedge; ++w) tab[3 * nb + w] = ((long long)wG * c->Nk + c->wedge_k[w]) * vs;
+  CKS(upload(c, c->d_w_items, w));
+  CKS(upload(c, c->d_dy_items, d));
+  CKS(upload(c, c->d_hf_tab, tab));
+  c->n_w_items = (int)w.size();
+  c->n_dy_items = (int)d.size();
+  c->tables = true;
+  return SGW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a4-a6: screened interaction
+// ---------------------------------------------------------------------------
+extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P0_tau, void* P_tau, sgw_stream stream) {
+  CKS(need_built(c));
+  if (!P0_tau || !P_tau) return SGW_ERR_ARG;
+  CKS(ensure_tables(c));
+  cudaStream_t st = S(stream);
+  const long long pe = c->p_elems;
   const int maxn = c->max_aux_block;
   const size_t wbytes = (size_t)2 * c->nwb * pe * sizeof(double2);
   const size_t scratch = maxn > 90 ? (size_t)304 * maxn * maxn * sizeof(double2) : 0;
-  CKS(ensure_workspace(c, wbytes + scratch + items.size() * sizeof(InvItem) + 4096));
+  CKS(ensure_workspace(c, wbytes + scratch + 4096));
   double2* P0w = c->d_ws;
   double2* Pw = P0w + (size_t)c->nwb * pe;
   double2* scr = Pw + (size_t)c->nwb * pe;
-  InvItem* d_items = reinterpret_cast<InvItem*>(scr + scratch / sizeof(double2));
-  CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(InvItem), cudaMemcpyHostToDevice, st));
   const double flt = 8.0 * c->nwb * (double)c->nt * pe;
   double flw = 0;
-  for (auto& it : items) flw += 8.0 * it.n * it.n * it.n;
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) flw += 8.0 * c->nwb * std::pow((double)c->auxb_n[b], 3);
   run(c, "ft", flt, 1, st, [&] {
     series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, z(1.0), 0, st);
   });
   run(c, "w_solve", flw, 1, st, [&] {
-    invert_blocks(INV_W, d_items, (int)items.size(), maxn, P0w, nullptr, nullptr, nullptr, 0.0, Pw, nullptr, scr,
-                  c->d_status, st);
+    invert_blocks(INV_W, c->d_w_items, c->n_w_items, maxn, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw,
+                  nullptr, scr, c->d_status, st);
   });
   run(c, "ft", flt, 1, st, [&] {
     series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, z(1.0), 0, st);
   });
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(st));
   return SGW_OK;
 }
 
@@ -844,8 +917,14 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
   P.unit_start.assign(nt + 1, 0);
   P.tile_start.assign(nt + 1, 0);
   long long base = 0;
+  double work_t = 0;
+  for (size_t b = 0; b < c->aob_off.size(); ++b) work_t += (double)c->aob_n[b] * c->aob_n[b] * c->naux * nao * Nk;
+  const long long target = unit_target(work_t * nc);
   for (int t = 0; t < nt; ++t) {
-    if (t % nc == 0) base = (long long)units.size();
+    if (t % nc == 0) {
+      if (t > 0) schedule_units(units, (size_t)base, 0);
+      base = (long long)units.size();
+    }
     P.unit_start[t] = units.size();
     P.tile_start[t] = tiles.size();
     const int tl = t % nc;
@@ -855,10 +934,11 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->g_elems + c->aob_off[b],
                      (p0 * nc + tl) * vs + (long long)st * nao, p0 * vs + (long long)st * nao, nao, nao, Nk,
-                     (long long)c->naux * nao);
+                     (long long)c->naux * nao, target);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
+  schedule_units(units, (size_t)base, 0);
   P.unit_start[nt] = units.size();
   P.tile_start[nt] = tiles.size();
   P.max_units_chunk = 0;
@@ -962,45 +1042,59 @@ static sgw_status density_matrix(sgw_ctx* c, const double2* G, double2* gamma, c
   return SGW_OK;
 }
 
+// Exchange plan: wedge points are processed in groups whose Z = V gamma intermediates fit the
+// workspace; one block multiply, one Gram launch and one reduction per group.
 static sgw_status build_k_plan(sgw_ctx* c) {
   ContractionPlan& P = c->plan_k;
   if (P.built) return SGW_OK;
   const int Nk = c->Nk, nw = c->nwedge, nao = c->nao;
   const long long vs = vsize(c);
+  const size_t budget = workspace_budget();
+  int grp = (int)std::max<long long>(1, (long long)(budget * 0.5 / ((double)Nk * vs * sizeof(double2))));
+  grp = std::min(grp, nw);
+  P.nc = grp;  // wedge points per group
   std::vector<BdItem> A;
   std::vector<GramUnit> units;
   std::vector<GramTile> tiles;
-  c->plan_k_wbeg.assign(nw + 1, 0);
-  c->plan_k_tbeg.assign(nw + 1, 0);
-  for (int w = 0; w < nw; ++w) {
-    c->plan_k_wbeg[w] = units.size();
-    c->plan_k_tbeg[w] = tiles.size();
-    for (int k2 = 0; k2 < Nk; ++k2) {
-      const long long p = (long long)w * Nk + k2;
-      BdItem x;
-      x.x_off = p * vs;
-      x.y_off = (long long)k2 * vs;
-      x.m_off = c->g_off[c->rep[k2]];
-      x.part = c->rep[k2];
-      x.pad = 0;
-      x.scale = z(1.0);
-      A.push_back(x);
-    }
+  c->plan_k_wbeg.clear();
+  c->plan_k_tbeg.clear();
+  for (int w0 = 0; w0 < nw; w0 += grp) {
+    const int w1 = std::min(nw, w0 + grp);
+    c->plan_k_wbeg.push_back(units.size());
+    c->plan_k_tbeg.push_back(tiles.size());
+    for (int w = w0; w < w1; ++w)
+      for (int k2 = 0; k2 < Nk; ++k2) {
+        const long long p = (long long)w * Nk + k2;
+        BdItem x;
+        x.x_off = p * vs;
+        x.y_off = (long long)((w - w0) * Nk + k2) * vs;
+        x.m_off = c->g_off[c->rep[k2]];
+        x.part = c->rep[k2];
+        x.pad = 0;
+        x.scale = z(1.0);
+        A.push_back(x);
+      }
+    double work = 0;
+    for (size_t b = 0; b < c->aob_off.size(); ++b)
+      if (c->aob_w[b] >= w0 && c->aob_w[b] < w1) work += (double)c->aob_n[b] * c->aob_n[b] * c->naux * nao * Nk;
+    const long long target = unit_target(work);
     const long long base = (long long)units.size();
     for (size_t b = 0; b < c->aob_off.size(); ++b) {
-      if (c->aob_w[b] != w) continue;
+      const int w = c->aob_w[b];
+      if (w < w0 || w >= w1) continue;
       const int nb = c->aob_n[b], st = c->aob_start[b];
       const size_t from = units.size();
-      add_gram_block(units, tiles, base, nb, c->aob_off[b], (long long)st * nao,
-                     (long long)w * Nk * vs + (long long)st * nao, nao, nao, Nk, (long long)c->naux * nao);
+      add_gram_block(units, tiles, base, nb, c->aob_off[b], (long long)(w - w0) * Nk * vs + (long long)st * nao,
+                     (long long)w * Nk * vs + (long long)st * nao, nao, nao, Nk, (long long)c->naux * nao, target);
       finalize_units(units, from, vs, vs);
     }
+    schedule_units(units, (size_t)base, 0);
   }
-  c->plan_k_wbeg[nw] = units.size();
-  c->plan_k_tbeg[nw] = tiles.size();
+  c->plan_k_wbeg.push_back(units.size());
+  c->plan_k_tbeg.push_back(tiles.size());
   P.max_units_chunk = 0;
-  for (int w = 0; w < nw; ++w)
-    P.max_units_chunk = std::max(P.max_units_chunk, c->plan_k_wbeg[w + 1] - c->plan_k_wbeg[w]);
+  for (size_t g = 0; g + 1 < c->plan_k_wbeg.size(); ++g)
+    P.max_units_chunk = std::max(P.max_units_chunk, c->plan_k_wbeg[g + 1] - c->plan_k_wbeg[g]);
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_units, units));
   CKS(upload(c, P.d_tiles, tiles));
@@ -1025,6 +1119,8 @@ static sgw_status build_k_plan(sgw_ctx* c) {
       u.r1 = 1;
       u.a_off = (long long)c->rep[kp] * nao * nao;
       u.b_off = ((long long)wG * Nk + kp) * vs + (long long)A0 * nao * nao;
+      u.slot = (int)ru.size();
+      u.pad = 0;
       ru.push_back(u);
     }
     rt.push_back(t);
@@ -1042,10 +1138,11 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
   if (!c->have_v[0] || !c->have_v[1]) return c->fail(SGW_ERR_STATE, "V not loaded");
   if (!G_tau || !Sigma_hf) return SGW_ERR_ARG;
   CKS(build_k_plan(c));
+  CKS(ensure_tables(c));
   cudaStream_t st = S(stream);
   const int Nk = c->Nk, nw = c->nwedge, nao = c->nao, naux = c->naux;
   const long long vs = vsize(c), mat = (long long)nao * nao;
-  const size_t zbytes = (size_t)Nk * vs;
+  const size_t zbytes = (size_t)c->plan_k.nc * Nk * vs;
   const size_t need = zbytes + (size_t)c->plan_k.max_units_chunk * 1024 + c->plan_rho.max_units_chunk * 1024 +
                       c->g_elems + (size_t)nw * mat + naux + 16 + c->aob_off.size() * 2 + nw + 64;
   CKS(ensure_workspace(c, need * sizeof(double2)));
@@ -1057,20 +1154,15 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
   double2* rho = gdense + (size_t)nw * mat;
   double2* out = static_cast<double2*>(Sigma_hf);
   density_matrix(c, static_cast<const double2*>(G_tau), gamma, st);
-  // dense gamma per wedge point for the Hartree density (tables in the workspace tail)
+  // dense gamma per wedge point for the Hartree density
   {
     const size_t nb = c->aob_off.size();
-    std::vector<long long> tab(2 * nb);
-    for (size_t b = 0; b < nb; ++b) {
-      tab[b] = c->aob_w[b] * mat + (long long)c->aob_start[b] * nao + c->aob_start[b];
-      tab[nb + b] = c->aob_off[b];
-    }
-    long long* d_tab = reinterpret_cast<long long*>(rho + naux + 8);
-    int* d_bn = reinterpret_cast<int*>(d_tab + 2 * nb);
-    CK(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_bn, c->aob_n.data(), nb * 4, cudaMemcpyHostToDevice, st));
+    const long long* d_tab = c->d_hf_tab;
+    const int* d_bn = reinterpret_cast<const int*>(d_tab + 2 * nb);
     run(c, "pack", 0.0, 1, st, [&] { fill_zero(gdense, (long long)nw * mat, st); });
-    run(c, "pack", 0.0, 1, st, [&] { pack_blocks(gdense, mat, nao, d_tab, d_bn, d_tab + nb, (int)nb, gamma, 0, st); });
+    run(c, "pack", 0.0, 1, st, [&] {
+      pack_blocks(gdense, mat, nao, d_tab, d_bn, d_tab + nb, (int)nb, gamma, 0, st);
+    });
   }
   // rho[A]
   GramGeom rg;
@@ -1088,11 +1180,7 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
   run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(c->plan_rho.d_tiles, (naux + 31) / 32, rpart, rho, z(1.0), 0, st); });
   // J^w_ij = (s/N_k) sum_A V^{k_w k_w}[A][i][j] rho[A]   (pair (Gamma, k_w) of orientation 0)
   {
-    std::vector<long long> vw(nw);
-    const int wG = c->rep[0];
-    for (int w = 0; w < nw; ++w) vw[w] = ((long long)wG * Nk + c->wedge_k[w]) * vs;
-    long long* d_vw = reinterpret_cast<long long*>(rho + naux + 8) + 2 * c->aob_off.size() + c->aob_off.size();
-    CK(cudaMemcpyAsync(d_vw, vw.data(), nw * 8, cudaMemcpyHostToDevice, st));
+    const long long* d_vw = c->d_hf_tab + 3 * c->aob_off.size();
     run(c, "hf_j", 8.0 * naux * (double)c->g_elems, 1, st, [&] {
       k_hartree<<<(unsigned)std::min<long long>(4096, (c->g_elems + 255) / 256), 256, 0, st>>>(
           c->d_V[0], rho, c->d_el_i, c->d_el_j, c->d_el_w, d_vw, c->g_elems, naux, nao,
@@ -1109,99 +1197,100 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
   gg.k_outer_b = mat;
   gg.k_inner = nao;
   gg.k_outer = naux;
-  for (int w = 0; w < nw; ++w) {
-    double flz = 0;
-    for (int k2 = 0; k2 < Nk; ++k2) flz += 8.0 * naux * nao * (double)c->part_ao[c->rep[k2]].elems;
+  const int grp = c->plan_k.nc;
+  for (size_t g = 0; g + 1 < c->plan_k_wbeg.size(); ++g) {
+    const int w0 = (int)g * grp, w1 = std::min(nw, w0 + grp);
+    double flz = 0, flg = 0;
+    for (int w = w0; w < w1; ++w) {
+      for (int k2 = 0; k2 < Nk; ++k2) flz += 8.0 * naux * nao * (double)c->part_ao[c->rep[k2]].elems;
+      flg += 8.0 * Nk * naux * nao * (double)c->part_ao[w].elems;
+    }
     run(c, "hf_k", flz, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), c->d_V[1], Zw, gamma, c->plan_k.d_A + (size_t)w * Nk, Nk,
-              c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), c->d_V[1], Zw, gamma, c->plan_k.d_A + (size_t)w0 * Nk,
+              (long long)(w1 - w0) * Nk, c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
     });
-    const long long u0 = c->plan_k_wbeg[w], u1 = c->plan_k_wbeg[w + 1];
-    const long long t0 = c->plan_k_tbeg[w], t1 = c->plan_k_tbeg[w + 1];
-    run(c, "hf_k", 8.0 * Nk * naux * nao * (double)c->part_ao[w].elems, 1, st, [&] {
+    const long long u0 = c->plan_k_wbeg[g], u1 = c->plan_k_wbeg[g + 1];
+    const long long t0 = c->plan_k_tbeg[g], t1 = c->plan_k_tbeg[g + 1];
+    run(c, "hf_k", flg, 1, st, [&] {
       gram_partials(gg, Zw, c->d_V[1], c->plan_k.d_units + u0, (int)(u1 - u0), part, st);
     });
-    run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(c->plan_k.d_tiles + t0, (int)(t1 - t0), part, out, z(-1.0 / Nk), 1, st); });
+    run(c, "gram_reduce", 0.0, 1, st, [&] {
+      gram_reduce(c->plan_k.d_tiles + t0, (int)(t1 - t0), part, out, z(-1.0 / Nk), 1, st);
+    });
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(st));
   return SGW_OK;
 }
 
 // ---------------------------------------------------------------------------
 // a8-a10: Dyson with the chemical-potential search
 // ---------------------------------------------------------------------------
-extern "C" SGW_API sgw_status sgw_dyson(sgw_ctx* c, const void* Sigma_tau, const void* Sigma_hf, double* mu_inout,
-                                        int search_mu, void* G_tau, sgw_stream stream) {
-  CKS(need_built(c));
-  if (!c->have_one_body) return c->fail(SGW_ERR_STATE, "one-body inputs not loaded");
-  if (!Sigma_tau || !Sigma_hf || !mu_inout || !G_tau) return SGW_ERR_ARG;
-  cudaStream_t st = S(stream);
+// Dyson for the whole wedge at one chemical potential, or with the bisection search of mu.
+// The search runs entirely on the device (no host round trip per trial): a fixed number of
+// trial launches whose later members do nothing once the search has stopped.  The final mu
+// is left in d_scalar[2].
+static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const double2* Sigma_hf, double mu,
+                               int search_mu, double2* G_tau, cudaStream_t st) {
+  CKS(ensure_tables(c));
   const long long ge = c->g_elems;
   const int nwf = c->nwf;
-  std::vector<InvItem> items;
-  for (int m = 0; m < nwf; ++m)
-    for (size_t b = 0; b < c->aob_off.size(); ++b) {
-      InvItem it;
-      it.a_off = (long long)m * ge + c->aob_off[b];
-      it.s_off = c->aob_off[b];
-      it.f_off = c->aob_off[b];
-      it.out_off = it.a_off;
-      it.n = c->aob_n[b];
-      it.m = m;
-      const double wk = (double)c->p.spin_factor / c->Nk * c->star[c->aob_w[b]];
-      it.weight = z(wk * c->gamma_w[m].real(), wk * c->gamma_w[m].imag());
-      items.push_back(it);
-    }
   const int maxn = c->max_ao_block;
   const size_t scratch = maxn > 90 ? (size_t)304 * maxn * maxn : 0;
-  const size_t need = (size_t)2 * nwf * ge + ge + scratch + items.size() + items.size() * sizeof(InvItem) / 16 + 64;
+  const size_t need = (size_t)2 * nwf * ge + ge + scratch + c->n_dy_items + 64;
   CKS(ensure_workspace(c, need * sizeof(double2)));
   double2* Sw = c->d_ws;
   double2* Gw = Sw + (size_t)nwf * ge;
   double2* F = Gw + (size_t)nwf * ge;
   double2* scr = F + ge;
   double2* tpart = scr + scratch;
-  InvItem* d_items = reinterpret_cast<InvItem*>(tpart + items.size() + 8);
-  CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(InvItem), cudaMemcpyHostToDevice, st));
-  // Sigma~(i w) and F = H0 + Sigma_HF
   double fli = 0;
-  for (auto& it : items) fli += 8.0 * it.n * it.n * it.n;
+  for (size_t b = 0; b < c->aob_n.size(); ++b) fli += 8.0 * nwf * std::pow((double)c->aob_n[b], 3);
   run(c, "ft", 8.0 * nwf * (double)c->nt * ge, 1, st, [&] {
-    series_map(c->d_TF, nwf, c->nt, static_cast<const double2*>(Sigma_tau), ge, Sw, ge, ge, z(1.0), 0, st);
+    series_map(c->d_TF, nwf, c->nt, Sigma_tau, ge, Sw, ge, ge, z(1.0), 0, st);
   });
   CK(cudaMemcpyAsync(F, c->d_H0, ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  run(c, "axpby", 0.0, 1, st, [&] { axpby(F, static_cast<const double2*>(Sigma_hf), ge, 1.0, 1.0, st); });
-  double mu = *mu_inout;
+  run(c, "axpby", 0.0, 1, st, [&] { axpby(F, Sigma_hf, ge, 1.0, 1.0, st); });
+  double* s = c->d_scalar;
+  double2* d_sum = reinterpret_cast<double2*>(c->d_scalar + 8);
+  const double* mu_dev = nullptr;
   if (search_mu) {
-    double lo = -20.0, hi = 20.0, mid = 0.0, nval = 0.0;
-    double2* d_sum = reinterpret_cast<double2*>(c->d_scalar);
+    run(c, "mu_search", 0.0, 1, st, [&] { mu_step(0, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
     for (int it = 0; it < 64; ++it) {
-      mid = 0.5 * (lo + hi);
+      run(c, "mu_search", 0.0, 1, st, [&] { mu_step(1, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
       run(c, "dyson_invert", fli, 1, st, [&] {
-        invert_blocks(INV_DYSON_TRACE, d_items, (int)items.size(), maxn, Sw, c->d_S, F, c->d_nu_f, mid, nullptr,
-                      tpart, scr, c->d_status, st);
+        invert_blocks(INV_DYSON_TRACE, c->d_dy_items, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f, 0.0, s + 2, s + 3,
+                      nullptr, tpart, scr, c->d_status, st);
       });
-      run(c, "reduce", 0.0, 1, st, [&] { sum_partials(tpart, (int)items.size(), d_sum, st); });
-      double2 h;
-      CK(cudaMemcpyAsync(&h, d_sum, sizeof(double2), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      nval = h.x;
-      if (std::fabs(nval - c->p.n_elec) <= 1e-11) break;
-      if (nval > c->p.n_elec) hi = mid; else lo = mid;
+      run(c, "reduce", 0.0, 1, st, [&] { sum_partials(tpart, c->n_dy_items, d_sum, st); });
+      run(c, "mu_search", 0.0, 1, st, [&] { mu_step(2, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
     }
-    mu = mid;
+    mu_dev = s + 2;
   }
   run(c, "dyson_invert", fli, 1, st, [&] {
-    invert_blocks(INV_DYSON_STORE, d_items, (int)items.size(), maxn, Sw, c->d_S, F, c->d_nu_f, mu, Gw, nullptr, scr,
-                  c->d_status, st);
+    invert_blocks(INV_DYSON_STORE, c->d_dy_items, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f, mu, mu_dev, nullptr,
+                  Gw, nullptr, scr, c->d_status, st);
   });
   run(c, "ft", 8.0 * nwf * (double)c->nt * ge, 1, st, [&] {
-    series_map(c->d_TFbar, c->nt, nwf, Gw, ge, static_cast<double2*>(G_tau), ge, ge, z(1.0), 0, st);
+    series_map(c->d_TFbar, c->nt, nwf, Gw, ge, G_tau, ge, ge, z(1.0), 0, st);
   });
   CK(cudaGetLastError());
-  *mu_inout = mu;
-  if (search_mu) return sgw_sync(c, stream);
+  return SGW_OK;
+}
+
+extern "C" SGW_API sgw_status sgw_dyson(sgw_ctx* c, const void* Sigma_tau, const void* Sigma_hf, double* mu_inout,
+                                        int search_mu, void* G_tau, sgw_stream stream) {
+  CKS(need_built(c));
+  if (!c->have_one_body) return c->fail(SGW_ERR_STATE, "one-body inputs not loaded");
+  if (!Sigma_tau || !Sigma_hf || !mu_inout || !G_tau) return SGW_ERR_ARG;
+  cudaStream_t st = S(stream);
+  CKS(dyson_device(c, static_cast<const double2*>(Sigma_tau), static_cast<const double2*>(Sigma_hf), *mu_inout,
+                   search_mu, static_cast<double2*>(G_tau), st));
+  if (search_mu) {
+    double mu = 0.0;
+    CK(cudaMemcpyAsync(&mu, c->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKS(sgw_sync(c, stream));
+    *mu_inout = mu;
+  }
   return SGW_OK;
 }
 
@@ -1279,64 +1368,110 @@ extern "C" SGW_API sgw_status sgw_energy(sgw_ctx* c, const void* G_tau, const vo
 // ---------------------------------------------------------------------------
 // a2..a12: iterate
 // ---------------------------------------------------------------------------
+// One pass, enqueued on `st` only (capturable): P0 -> P -> Sigma~, Sigma_HF -> damping ->
+// max |Delta Sigma| -> Dyson with the device-side mu search; the scalars the host needs
+// (mu, N, max |Delta Sigma|) are copied into pinned host memory at the end of the pass.
+static sgw_status iteration_body(sgw_ctx* c, double damping, double2* G, double2* Sig, double2* Hf, cudaStream_t st) {
+  const long long ge = c->g_elems;
+  const int nt = c->nt;
+  sgw_stream ss = reinterpret_cast<sgw_stream>(st);
+  CKS(sgw_polarization(c, G, c->d_it_P0, ss));
+  CKS(sgw_screened_interaction(c, c->d_it_P0, c->d_it_P, ss));
+  CKS(sgw_self_energy(c, G, c->d_it_P, c->d_it_S, ss));
+  CKS(sgw_hartree_fock(c, G, c->d_it_H, ss));
+  // Sigma <- (1 - a) Sigma_old + a Sigma_new, and max |Sigma_damped - Sigma_old|
+  run(c, "axpby", 0.0, 1, st, [&] { axpby(c->d_it_S, Sig, (long long)nt * ge, damping, 1.0 - damping, st); });
+  run(c, "axpby", 0.0, 1, st, [&] { axpby(c->d_it_H, Hf, ge, damping, 1.0 - damping, st); });
+  run(c, "reduce", 0.0, 1, st, [&] { max_abs_diff(c->d_it_S, Sig, (long long)nt * ge, c->d_maxbits, st); });
+  run(c, "reduce", 0.0, 1, st, [&] { max_abs_diff(c->d_it_H, Hf, ge, c->d_maxbits + 1, st); });
+  CK(cudaMemcpyAsync(Sig, c->d_it_S, (size_t)nt * ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(Hf, c->d_it_H, (size_t)ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CKS(dyson_device(c, Sig, Hf, 0.0, 1, G, st));
+  CK(cudaMemcpyAsync(c->h_pinned, c->d_scalar, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->h_pinned + 8, c->d_maxbits, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  return SGW_OK;
+}
+
+static bool graphs_enabled() {
+  const char* e = std::getenv("SGW_GRAPH");
+  return !(e && e[0] == '0');
+}
+
 extern "C" SGW_API sgw_status sgw_iterate(sgw_ctx* c, int max_iter, double damping, double tol, void* G_tau,
                                           void* Sigma_tau, void* Sigma_hf, double* mu, sgw_iter_stats* stats,
                                           sgw_stream stream) {
   CKS(need_built(c));
   if (!G_tau || !Sigma_tau || !Sigma_hf || !mu || max_iter < 1 || !(damping > 0) || damping > 1)
     return SGW_ERR_ARG;
+  if (!c->have_one_body || !c->have_v[0] || !c->have_v[1]) return c->fail(SGW_ERR_STATE, "inputs not loaded");
   cudaStream_t st = S(stream);
   const long long ge = c->g_elems, pe = c->p_elems;
   const int nt = c->nt;
-  // persistent buffers for P0, P and the new Sigma (outside the shared workspace)
-  double2 *P0 = nullptr, *Pt = nullptr, *Sn = nullptr, *Hn = nullptr;
-  if (cudaMalloc(&P0, (size_t)nt * pe * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&Pt, (size_t)nt * pe * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&Sn, (size_t)nt * ge * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&Hn, (size_t)ge * sizeof(double2)) != cudaSuccess) {
-    cudaFree(P0); cudaFree(Pt); cudaFree(Sn); cudaFree(Hn);
-    return c->fail(SGW_ERR_OOM, "iteration buffers");
+  if (!c->d_it_P0) {
+    if (cudaMalloc(&c->d_it_P0, (size_t)nt * pe * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->d_it_P, (size_t)nt * pe * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->d_it_S, (size_t)nt * ge * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->d_it_H, (size_t)ge * sizeof(double2)) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned, 16 * sizeof(double)) != cudaSuccess)
+      return c->fail(SGW_ERR_OOM, "iteration buffers");
   }
-  sgw_status s = SGW_OK;
+  double2* G = static_cast<double2*>(G_tau);
+  double2* Sig = static_cast<double2*>(Sigma_tau);
+  double2* Hf = static_cast<double2*>(Sigma_hf);
+  // a graph needs a capturable (non-legacy) stream and no per-kernel event timing
+  const bool graph = graphs_enabled() && st != nullptr && !c->prof_on && c->it_warm;
+  if (graph && (c->it_exec == nullptr || c->it_key[0] != G || c->it_key[1] != Sig || c->it_key[2] != Hf ||
+                c->it_damping != damping || c->it_gen != c->ws_gen)) {
+    if (c->it_exec) cudaGraphExecDestroy(c->it_exec);
+    if (c->it_graph) cudaGraphDestroy(c->it_graph);
+    c->it_exec = nullptr;
+    c->it_graph = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    sgw_status sb = iteration_body(c, damping, G, Sig, Hf, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (sb != SGW_OK) {
+      if (g) cudaGraphDestroy(g);
+      return sb;
+    }
+    if (ec != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    c->it_graph = g;
+    CK(cudaGraphInstantiate(&c->it_exec, g, 0));
+    c->it_key[0] = G;
+    c->it_key[1] = Sig;
+    c->it_key[2] = Hf;
+    c->it_damping = damping;
+    c->it_gen = c->ws_gen;
+  }
   double dmax = 0.0;
   int it = 0;
   for (it = 0; it < max_iter; ++it) {
-    if ((s = sgw_polarization(c, G_tau, P0, stream)) != SGW_OK) break;
-    if ((s = sgw_screened_interaction(c, P0, Pt, stream)) != SGW_OK) break;
-    if ((s = sgw_self_energy(c, G_tau, Pt, Sn, stream)) != SGW_OK) break;
-    if ((s = sgw_hartree_fock(c, G_tau, Hn, stream)) != SGW_OK) break;
-    // Sigma <- (1 - a) Sigma_old + a Sigma_new ; record max |Sigma_new_damped - Sigma_old|
-    run(c, "axpby", 0.0, 1, st, [&] { axpby(Sn, static_cast<double2*>(Sigma_tau), (long long)nt * ge, damping, 1.0 - damping, st); });
-    run(c, "axpby", 0.0, 1, st, [&] { axpby(Hn, static_cast<double2*>(Sigma_hf), ge, damping, 1.0 - damping, st); });
-    unsigned long long b1 = 0, b2 = 0;
-    run(c, "reduce", 0.0, 1, st, [&] { max_abs_diff(Sn, static_cast<double2*>(Sigma_tau), (long long)nt * ge, c->d_maxbits, st); });
-    cudaMemcpyAsync(&b1, c->d_maxbits, 8, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    run(c, "reduce", 0.0, 1, st, [&] { max_abs_diff(Hn, static_cast<double2*>(Sigma_hf), ge, c->d_maxbits, st); });
-    cudaMemcpyAsync(&b2, c->d_maxbits, 8, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    if (graph) {
+      CK(cudaGraphLaunch(c->it_exec, st));
+    } else {
+      CKS(iteration_body(c, damping, G, Sig, Hf, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    c->it_warm = 1;
     double d1, d2;
-    std::memcpy(&d1, &b1, 8);
-    std::memcpy(&d2, &b2, 8);
+    std::memcpy(&d1, c->h_pinned + 8, 8);
+    std::memcpy(&d2, c->h_pinned + 9, 8);
     dmax = std::max(d1, d2);
-    cudaMemcpyAsync(Sigma_tau, Sn, (size_t)nt * ge * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(Sigma_hf, Hn, (size_t)ge * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-    if ((s = sgw_dyson(c, Sigma_tau, Sigma_hf, mu, 1, G_tau, stream)) != SGW_OK) break;
+    *mu = c->h_pinned[2];
     if (dmax < tol) { ++it; break; }
   }
-  if (s == SGW_OK && stats) {
+  CKS(sgw_sync(c, stream));
+  if (stats) {
     stats->iterations = it;
     stats->mu = *mu;
     stats->max_dsigma = dmax;
+    stats->n_elec = c->h_pinned[4];
     double e[5];
-    s = sgw_energy(c, G_tau, Sigma_hf, Sigma_tau, e, stream);
+    CKS(sgw_energy(c, G_tau, Sigma_hf, Sigma_tau, e, stream));
     for (int i = 0; i < 4; ++i) stats->energy[i] = e[i];
     stats->energy_imag = e[4];
-    stats->n_elec = c->p.n_elec;
   }
-  cudaStreamSynchronize(st);
-  cudaFree(P0); cudaFree(Pt); cudaFree(Sn); cudaFree(Hn);
-  return s;
+  return SGW_OK;
 }
 
 // ---------------------------------------------------------------------------

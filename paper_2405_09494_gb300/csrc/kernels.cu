@@ -7,6 +7,7 @@
 // and read operands through L1/shared memory with coalesced rows.
 #include <cfloat>
 #include <cstdio>
+#include <type_traits>
 
 #include "sgw_internal.h"
 
@@ -172,62 +173,91 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __re
   const int KC = gram_chunk(rmax);
   const int LD = KC + 1;
   const int mn = u.rows_m * u.rows_n;
-  const bool big = mn > 256;
-  const int P = big ? 1 : 256 / mn;
-  const int em = big ? 0 : (tid % mn) / u.rows_n;
-  const int en = big ? 0 : (tid % mn) % u.rows_n;
-  const int kp = big ? 0 : tid / mn;
-  const int ty = tid >> 4, tx = tid & 15;
-  Z acc0 = czero<Z>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+  // Every lane works on a real output: up to 4 outputs per thread for large tiles,
+  // K split over P phases for small ones.  No padded rows are ever multiplied.
+  const int P = mn >= 256 ? 1 : 256 / mn;
+  const int kp = tid / (mn < 256 ? mn : 256);
+  const int nown = mn >= 256 ? (mn - tid + 255) / 256 : (kp < P ? 1 : 0);
+  int em[4], en[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = (mn >= 256 ? tid + 256 * i : tid % mn);
+    em[i] = e / u.rows_n;
+    en[i] = e - em[i] * u.rows_n;
+  }
+  Z acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = czero<Z>();
   const int K = g.k_inner * g.k_outer;
-  const int nload = rmax * KC;
   for (int r = u.r0; r < u.r1; ++r) {
     const Z* Ap = A + u.a_off + (long long)(r - u.r0) * g.a_pair;
     const Z* Bp = B + u.b_off + (long long)(r - u.r0) * g.b_pair;
     for (int k0 = 0; k0 < K; k0 += KC) {
-      for (int idx = tid; idx < nload; idx += 256) {
+      for (int idx = tid; idx < rmax * KC; idx += 256) {
         const int i = idx / KC, kk = idx - i * KC;
         const int k = k0 + kk;
-        Z va = czero<Z>(), vb = va;
         if (k < K) {
           const int ko = k / g.k_inner, ki = k - ko * g.k_inner;
-          if (i < u.rows_m) va = Ap[(long long)i * g.a_row + (long long)ko * g.k_outer_a + ki];
-          if (i < u.rows_n) vb = Bp[(long long)i * g.b_row + (long long)ko * g.k_outer_b + ki];
+          if (i < u.rows_m) As[i * LD + kk] = Ap[(long long)i * g.a_row + (long long)ko * g.k_outer_a + ki];
+          if (i < u.rows_n) Bs[i * LD + kk] = Bp[(long long)i * g.b_row + (long long)ko * g.k_outer_b + ki];
+        } else {
+          if (i < u.rows_m) As[i * LD + kk] = czero<Z>();
+          if (i < u.rows_n) Bs[i * LD + kk] = czero<Z>();
         }
-        As[i * LD + kk] = va;
-        Bs[i * LD + kk] = vb;
       }
       __syncthreads();
-      if (big) {
-        // 2x2 micro tile: rows ty, ty+16; columns tx, tx+16
-#pragma unroll 4
-        for (int kk = 0; kk < KC; ++kk) {
-          const Z a0 = As[ty * LD + kk], a1 = As[(ty + 16) * LD + kk];
-          const Z b0 = Bs[tx * LD + kk], b1 = Bs[(tx + 16) * LD + kk];
-          acc0 = cfma_cj(a0, b0, acc0);
-          acc1 = cfma_cj(a0, b1, acc1);
-          acc2 = cfma_cj(a1, b0, acc2);
-          acc3 = cfma_cj(a1, b1, acc3);
+      const int kend = (K - k0) < KC ? (K - k0) : KC;
+      if (std::is_same<Z, float2>::value && mn >= 256) {
+        // single precision: 2x2 register tile (rows ty, ty+16; columns tx, tx+16) halves the shared loads
+        const int ty = tid >> 4, tx = tid & 15;
+        const bool m0 = ty < u.rows_m, m1 = ty + 16 < u.rows_m, n0 = tx < u.rows_n, n1 = tx + 16 < u.rows_n;
+        for (int kk = 0; kk < kend; ++kk) {
+          const Z a0 = m0 ? As[ty * LD + kk] : czero<Z>(), a1 = m1 ? As[(ty + 16) * LD + kk] : czero<Z>();
+          const Z b0 = n0 ? Bs[tx * LD + kk] : czero<Z>(), b1 = n1 ? Bs[(tx + 16) * LD + kk] : czero<Z>();
+          acc[0] = cfma_cj(a0, b0, acc[0]);
+          acc[1] = cfma_cj(a0, b1, acc[1]);
+          acc[2] = cfma_cj(a1, b0, acc[2]);
+          acc[3] = cfma_cj(a1, b1, acc[3]);
+        }
+      } else if (mn >= 256) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (i < nown) {
+            const Z* ar = As + em[i] * LD;
+            const Z* br = Bs + en[i] * LD;
+            Z a = acc[i];
+            for (int kk = 0; kk < kend; ++kk) a = cfma_cj(ar[kk], br[kk], a);
+            acc[i] = a;
+          }
         }
       } else if (kp < P) {
-        for (int kk = kp; kk < KC; kk += P) acc0 = cfma_cj(As[em * LD + kk], Bs[en * LD + kk], acc0);
+        const Z* ar = As + em[0] * LD;
+        const Z* br = Bs + en[0] * LD;
+        Z a = acc[0];
+        for (int kk = kp; kk < kend; kk += P) a = cfma_cj(ar[kk], br[kk], a);
+        acc[0] = a;
       }
       __syncthreads();
     }
   }
-  Z* out = partial + (long long)blockIdx.x * 1024;
-  if (big) {
-    if (ty < u.rows_m && tx < u.rows_n) out[ty * 32 + tx] = acc0;
-    if (ty < u.rows_m && tx + 16 < u.rows_n) out[ty * 32 + tx + 16] = acc1;
-    if (ty + 16 < u.rows_m && tx < u.rows_n) out[(ty + 16) * 32 + tx] = acc2;
-    if (ty + 16 < u.rows_m && tx + 16 < u.rows_n) out[(ty + 16) * 32 + tx + 16] = acc3;
+  Z* out = partial + (long long)u.slot * 1024;
+  if (std::is_same<Z, float2>::value && mn >= 256) {
+    const int ty = tid >> 4, tx = tid & 15;
+    if (ty < u.rows_m && tx < u.rows_n) out[ty * 32 + tx] = acc[0];
+    if (ty < u.rows_m && tx + 16 < u.rows_n) out[ty * 32 + tx + 16] = acc[1];
+    if (ty + 16 < u.rows_m && tx < u.rows_n) out[(ty + 16) * 32 + tx] = acc[2];
+    if (ty + 16 < u.rows_m && tx + 16 < u.rows_n) out[(ty + 16) * 32 + tx + 16] = acc[3];
+  } else if (mn >= 256) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < nown) out[em[i] * 32 + en[i]] = acc[i];
   } else {
-    red[tid] = acc0;
+    red[tid] = acc[0];
     __syncthreads();
     if (tid < mn) {
       Z s = czero<Z>();
       for (int p = 0; p < P; ++p) s = cadd(s, red[p * mn + tid]);
-      out[em * 32 + en] = s;
+      out[em[0] * 32 + en[0]] = s;
     }
   }
 }
@@ -324,9 +354,12 @@ constexpr int kInvSmemMaxN = 90;
 __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restrict__ items, int nitems, int max_n,
                                                 const double2* __restrict__ Asrc, const double2* __restrict__ S,
                                                 const double2* __restrict__ F, const double* __restrict__ nu,
-                                                double mu, double2* __restrict__ out, double2* __restrict__ tpart,
-                                                double2* __restrict__ scratch, int* __restrict__ status,
-                                                int use_smem) {
+                                                double mu_host, const double* __restrict__ mu_dev,
+                                                const double* __restrict__ done_dev, double2* __restrict__ out,
+                                                double2* __restrict__ tpart, double2* __restrict__ scratch,
+                                                int* __restrict__ status, int use_smem) {
+  if (done_dev != nullptr && *done_dev != 0.0) return;  // a finished search skips its remaining trials
+  const double mu = mu_dev != nullptr ? *mu_dev : mu_host;
   extern __shared__ double2 smem[];
   __shared__ double2 col[640];
   __shared__ int perm[640];
@@ -449,8 +482,8 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
 }
 
 void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
-                   const double2* F, const double* nu, double mu, double2* out, double2* trace_partial,
-                   double2* scratch, int* status, cudaStream_t st) {
+                   const double2* F, const double* nu, double mu, const double* mu_dev, const double* done_dev,
+                   double2* out, double2* trace_partial, double2* scratch, int* status, cudaStream_t st) {
   if (nitems <= 0) return;
   const int use_smem = max_n <= kInvSmemMaxN ? 1 : 0;
   const size_t sm = use_smem ? (size_t)max_n * max_n * sizeof(double2) : 0;
@@ -462,8 +495,8 @@ void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const 
   }
   int grid = nitems;
   if (!use_smem && grid > 304) grid = 304;  // one scratch slot per resident CTA
-  k_invert<<<grid, 256, sm, st>>>(mode, items, nitems, max_n, A, S, F, nu, mu, out, trace_partial, scratch, status,
-                                  use_smem);
+  k_invert<<<grid, 256, sm, st>>>(mode, items, nitems, max_n, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial,
+                                  scratch, status, use_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -788,6 +821,29 @@ void g0_closed_form(const double2* C, const double* eps, const long long* row_bo
                     double2* G, cudaStream_t st) {
   k_g0<<<grid_for(g_elems * ntau, 256, 8192), 256, 0, st>>>(C, eps, row_boff, row_bn, row_eoff, g_elems, tau, ntau,
                                                               beta, mu, G);
+}
+
+// One step of the chemical-potential bisection, decided on the device.  s[0] lo, s[1] hi,
+// s[2] mu (the trial), s[3] done, s[4] N of the last trial.  mode 0: start the search on
+// [lo, hi]; mode 1: new trial mu = (lo + hi) / 2 unless done; mode 2: read N(mu) and either
+// stop (|N - target| <= tol) or halve the bracket (N > target: hi = mu, else lo = mu).
+__global__ void k_mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (mode == 0) {
+    s[0] = lo; s[1] = hi; s[2] = 0.5 * (lo + hi); s[3] = 0.0; s[4] = 0.0;
+  } else if (mode == 1) {
+    if (s[3] == 0.0) s[2] = 0.5 * (s[0] + s[1]);
+  } else if (s[3] == 0.0) {
+    const double n = nsum->x;
+    s[4] = n;
+    if (fabs(n - target) <= tol) s[3] = 1.0;
+    else if (n > target) s[1] = s[2];
+    else s[0] = s[2];
+  }
+}
+void mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi,
+             cudaStream_t st) {
+  k_mu_step<<<1, 32, 0, st>>>(mode, s, nsum, target, tol, lo, hi);
 }
 
 // mu by bisection on (sum_i w_i f(eps_i - mu)) = target, one CTA, fixed 200 halvings.

@@ -42,6 +42,8 @@ struct GramUnit {
   long long a_off, b_off;  // element offsets (pair r0, first tile row) of the A and B operands
   int rows_m, rows_n;      // tile extent
   int r0, r1;              // pair range [r0, r1)
+  int slot;                // partial-sum slot (units run largest first; tiles address slots)
+  int pad;
 };
 
 // Output tile of a Gram reduction: sums its units (in order) into the packed output.
@@ -99,8 +101,10 @@ struct InvItem {
 };
 enum InvMode { INV_W = 0, INV_DYSON_STORE = 1, INV_DYSON_TRACE = 2 };
 void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
-                   const double2* F, const double* nu, double mu, double2* out, double2* trace_partial,
-                   double2* scratch, int* status, cudaStream_t st);
+                   const double2* F, const double* nu, double mu, const double* mu_dev, const double* done_dev,
+                   double2* out, double2* trace_partial, double2* scratch, int* status, cudaStream_t st);
+void mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi,
+             cudaStream_t st);
 
 // Batched generalised Hermitian eigensolver H C = S C eps (S may be null: identity).
 struct EigItem {
@@ -205,6 +209,20 @@ struct sgw_ctx {
   // block lists over the wedge: orbital and auxiliary
   std::vector<long long> aob_off, auxb_off;  // packed offset
   std::vector<int> aob_n, auxb_n, aob_w, auxb_w, aob_start, auxb_start;
+  // static launch tables of the hot path (built once, so the iteration can be captured in a graph)
+  bool tables = false;
+  sgw::InvItem *d_w_items = nullptr, *d_dy_items = nullptr;
+  int n_w_items = 0, n_dy_items = 0;
+  long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
+  // iteration buffers and the captured graph
+  double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
+  double* h_pinned = nullptr;  // host-visible scalars written at the end of a captured iteration
+  cudaGraphExec_t it_exec = nullptr;
+  cudaGraph_t it_graph = nullptr;
+  const void* it_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  double it_damping = -1.0;
+  long long it_gen = -1, ws_gen = 0;  // workspace generation seen by the captured graph
+  int it_warm = 0;
   double2* d_C0 = nullptr;   // eigenvectors of (H0, S) per block (packed)
   double* d_eps0 = nullptr;  // eigenvalues [nwedge][nao]
   double* d_epsw = nullptr;  // weight per eigenvalue (s / N_k * star)

@@ -176,3 +176,57 @@ def test_diamond_nonsymmorphic_chain(diamond):
     assert rel_err(diamond.unf(1, diamond.lP), diamond.P) < TOL
     assert rel_err(diamond.unf(0, diamond.lSig), diamond.Sig) < TOL
     assert rel_err(diamond.unf(0, diamond.lShf), diamond.Shf) < TOL
+
+
+# ------------------------------------------------------------------ one full pass (sgw_iterate)
+def test_c1_fine_full_iteration_matches_oracle(c1_fine):
+    """One pass of sgw_iterate (damping, mu search) against the oracle's scgw_iteration from G0."""
+    import torch
+
+    from paper_2405_09494_gb300 import sgw
+
+    c = c1_fine
+    s = c.sess.sys
+    cfg = c.cfg
+    Z0 = np.zeros_like(c.Sig)
+    H0 = np.zeros_like(c.Shf)
+    ref = gw.scgw_iteration(s.H0, s.S, c.V, cfg.nk, c.G0, c.mu0, c.og, cfg.n_elec, cfg.spin, cfg.loop_sign,
+                            search_mu=True, Sigma_old=Z0, Sigma_hf_old=H0, damping=0.5)
+    G, mu0 = c.sess.g0()
+    Sig = c.sess.g_series()
+    Shf = c.sess.zeros(c.sess.layout.g_elems)
+    stream = torch.cuda.Stream()
+    mu, stats = sgw.sgw_iterate(c.sess.ctx, 1, 0.5, 0.0, G, Sig, Shf, mu0, stream)
+    torch.cuda.synchronize()
+    assert abs(mu - ref["mu"]) < 1e-9
+    assert rel_err(c.unf(0, Sig), ref["Sigma"]) < TOL
+    assert rel_err(c.unf(0, Shf), ref["Sigma_hf"]) < TOL
+    assert rel_err(c.unf(0, G), ref["G_new"]) < TOL
+    assert stats.iterations == 1
+
+
+def test_graph_replay_equals_direct_launches(c1_fine):
+    """Three passes replayed from the captured CUDA graph equal three passes of direct launches."""
+    import os
+
+    import torch
+
+    from paper_2405_09494_gb300 import sgw
+
+    def run(graph):
+        os.environ["SGW_GRAPH"] = "1" if graph else "0"
+        try:
+            G, mu = c1_fine.sess.g0()
+            Sig = c1_fine.sess.g_series()
+            Shf = c1_fine.sess.zeros(c1_fine.sess.layout.g_elems)
+            stream = torch.cuda.Stream()
+            for _ in range(3):
+                mu, _ = sgw.sgw_iterate(c1_fine.sess.ctx, 1, 0.5, 0.0, G, Sig, Shf, mu, stream)
+            torch.cuda.synchronize()
+            return to_np(G), to_np(Sig), mu
+        finally:
+            os.environ.pop("SGW_GRAPH", None)
+
+    Ga, Sa, ma = run(False)
+    Gb, Sb, mb = run(True)
+    assert np.array_equal(Ga, Gb) and np.array_equal(Sa, Sb) and ma == mb
