@@ -27,6 +27,11 @@ B50 = [-196, -91, -54, -38, -30, -25, -21, -19, -17, -16, -15, -14, -13, -12, -1
 F16 = [-15, -8, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 7, 14]
 B16 = [-21, -10, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 10, 21]
 
+F100 = [-529, -268, -177, -132, -106, -88, -76, -67, -60, -54, -50, -46, -43, -40, -38, -36, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 35, 37, 39, 42, 45, 49, 53, 59, 66, 75, 87, 105, 131, 176, 267, 528]
+B100 = [-775, -358, -212, -150, -116, -95, -81, -70, -62, -56, -51, -47, -44, -41, -39, -37, -35, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 35, 37, 39, 41, 44, 47, 51, 56, 62, 70, 81, 95, 116, 150, 212, 358, 775]
+F150 = [-1174, -593, -392, -292, -233, -194, -166, -146, -130, -117, -107, -98, -91, -85, -80, -75, -71, -68, -65, -62, -59, -57, -55, -53, -52, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 51, 52, 54, 56, 58, 61, 64, 67, 70, 74, 79, 84, 90, 97, 106, 116, 129, 145, 165, 193, 232, 291, 391, 592, 1173]
+B150 = [-1735, -802, -474, -335, -259, -211, -179, -155, -137, -123, -111, -102, -94, -88, -82, -77, -73, -69, -66, -63, -60, -58, -56, -54, -52, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 50, 52, 54, 56, 58, 60, 63, 66, 69, 73, 77, 82, 88, 94, 102, 111, 123, 137, 155, 179, 211, 259, 335, 474, 802, 1735]
+
 
 @dataclass
 class Config:
@@ -84,6 +89,14 @@ CONFIGS = {
         name="c2", index=1, structure="rocksalt", nk=(3, 3, 3), ao_shells=_shells({0: 1, 1: 1, 2: 1}),
         aux_shells=_shells({0: 6, 1: 5, 2: 3, 3: 2}), ntau=50, beta=100.0, mats_f=F50, mats_b=B50,
         description="rocksalt Oh, 3x3x3 mesh (4 wedge points), nao 18, naux 100, 50 tau, beta 100"),
+    "c3": Config(
+        name="c3", index=2, structure="rocksalt", nk=(4, 4, 4), ao_shells=_shells({0: 4, 1: 4, 2: 2}),
+        aux_shells=_shells({0: 10, 1: 10, 2: 11, 3: 4, 4: 3}), ntau=100, beta=200.0, mats_f=F100, mats_b=B100,
+        description="rocksalt Oh, 4x4x4 mesh (8 wedge points), nao 52, naux 300, 100 tau, beta 200"),
+    "c4": Config(
+        name="c4", index=3, structure="diamond", nk=(4, 4, 4), ao_shells=_shells({0: 4, 1: 4, 2: 2}),
+        aux_shells=_shells({0: 10, 1: 10, 2: 11, 3: 4, 4: 3}), ntau=150, beta=200.0, mats_f=F150, mats_b=B150,
+        description="diamond Fd-3m (non-symmorphic), 4x4x4 mesh (8 wedge points), nao 52, naux 300, 150 tau, beta 200"),
     # small rocksalt cell for the smoke run and the fast parity tests: 2x2x2 mesh (3 wedge points)
     "t1": Config(
         name="t1", index=10, structure="rocksalt", nk=(2, 2, 2), ao_shells=(0, 1), aux_shells=(0, 0, 1, 2),

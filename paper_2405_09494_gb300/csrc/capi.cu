@@ -147,6 +147,14 @@ static void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
   c->prof_pending.push_back({id, a, b});
 }
 
+// Chunked block multiply over the orbital (kind 0) or auxiliary (kind 1) partitions.
+template <typename Z>
+static void bdm(sgw_ctx* c, int kind, const BdGeom& g, const Z* X, Z* Y, const Z* M, const BdItem* items,
+                long long nitems, cudaStream_t st) {
+  bd_mult2(g, X, Y, M, items, nitems, c->d_nunits[kind], c->d_units[kind], c->d_udoff[kind], c->ustride[kind],
+           c->ustride[kind], st);
+}
+
 // Build the block-diagonal multiply geometry for a [U][Vd][Wd] contiguous tensor.
 static BdGeom geom(int U, int Vd, int Wd, int left, int trans, int conj, int accumulate, int n_part) {
   BdGeom g;
@@ -309,6 +317,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_ao_start); dfree(c->d_ao_size); dfree(c->d_ao_doff);
   dfree(c->d_aux_start); dfree(c->d_aux_size); dfree(c->d_aux_doff);
   dfree(c->d_full_start); dfree(c->d_full_size); dfree(c->d_full_doff);
+  for (int b = 0; b < 2; ++b) { dfree(c->d_nunits[b]); dfree(c->d_units[b]); dfree(c->d_udoff[b]); }
   dfree(c->d_V[0]); dfree(c->d_V[1]); dfree(c->d_V32[0]); dfree(c->d_V32[1]); dfree(c->d_H0); dfree(c->d_S);
   dfree(c->d_el_boff); dfree(c->d_el_eoff); dfree(c->d_el_bn); dfree(c->d_el_i); dfree(c->d_el_j); dfree(c->d_el_w);
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
@@ -364,6 +373,38 @@ extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_struct
   }
   CKS(upload(c, c->d_ao_start, s0)); CKS(upload(c, c->d_ao_size, z0)); CKS(upload(c, c->d_ao_doff, d0));
   CKS(upload(c, c->d_aux_start, s1)); CKS(upload(c, c->d_aux_size, z1)); CKS(upload(c, c->d_aux_doff, d1));
+  // chunked unit tables: every block split into runs of at most 8 outputs
+  for (int b = 0; b < 2; ++b) {
+    const auto& parts = b == 0 ? c->part_ao : c->part_aux;
+    std::vector<std::vector<int4>> lists(nw);
+    std::vector<std::vector<long long>> doffs(nw);
+    int stride = 1;
+    for (int w = 0; w < nw; ++w) {
+      int st0 = 0;
+      long long d0 = 0;
+      for (int sz : parts[w].sizes) {
+        for (int f = 0; f < sz; f += 8) {
+          lists[w].push_back(make_int4(st0 + f, std::min(8, sz - f), st0, sz));
+          doffs[w].push_back(d0);
+        }
+        st0 += sz;
+        d0 += (long long)sz * sz;
+      }
+      stride = std::max(stride, (int)lists[w].size());
+    }
+    std::vector<int> nu(nw);
+    std::vector<int4> un((size_t)nw * stride, make_int4(0, 0, 0, 1));
+    std::vector<long long> ud((size_t)nw * stride, 0);
+    for (int w = 0; w < nw; ++w) {
+      nu[w] = (int)lists[w].size();
+      std::copy(lists[w].begin(), lists[w].end(), un.begin() + (size_t)w * stride);
+      std::copy(doffs[w].begin(), doffs[w].end(), ud.begin() + (size_t)w * stride);
+    }
+    CKS(upload(c, c->d_nunits[b], nu));
+    CKS(upload(c, c->d_units[b], un));
+    CKS(upload(c, c->d_udoff[b], ud));
+    c->ustride[b] = stride;
+  }
   const int W = std::max(nao, naux);
   std::vector<int> fs(2 * W, 0), fz(2 * W, 0);
   std::vector<long long> fd(2 * W, 0);
@@ -751,13 +792,11 @@ static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2*
     const int ntc = t1 - t0;
     // Z[A][c][j] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
     run(c, t_vg.c_str(), P.fl_A_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, Zw, G, P.d_A + (size_t)t0 * np, ni, c->d_ao_start,
-              c->d_ao_size, c->d_ao_doff, st);
+      bdm(c, 0, geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, Zw, G, P.d_A + (size_t)t0 * np, ni, st);
     });
     // X[A][i][j] = sum_c G^k(-tau)[i][c] Z[A][c][j]
     run(c, t_gvg.c_str(), P.fl_B_t * ntc, 1, st, [&] {
-      bd_mult(geom(naux, nao, nao, 1, 0, 0, 0, nao), Zw, X, G, P.d_B + (size_t)t0 * np, ni, c->d_ao_start,
-              c->d_ao_size, c->d_ao_doff, st);
+      bdm(c, 0, geom(naux, nao, nao, 1, 0, 0, 0, nao), Zw, X, G, P.d_B + (size_t)t0 * np, ni, st);
     });
     const long long u0 = P.unit_start[t0], u1 = P.unit_start[t1];
     const long long ti0 = P.tile_start[t0], ti1 = P.tile_start[t1];
@@ -828,6 +867,19 @@ static sgw_status ensure_tables(sgw_ctx* c) {
   for (size_t b = 0; b < nb; ++b) bn[b] = c->aob_n[b];
   const int wG = c->rep[0];
   for (int w = 0; w < c->nwedge; ++w) tab[3 * nb + w] = ((long long)wG * c->Nk + c->wedge_k[w]) * vs;
+  // warp-sized blocks first (one warp each), larger blocks after (one CTA each); slots keep the
+  // original order so the trace partials are summed in a fixed order
+  auto split = [](std::vector<InvItem>& v, int& max_small) {
+    for (size_t i = 0; i < v.size(); ++i) v[i].slot = (int)i;
+    std::stable_partition(v.begin(), v.end(), [](const InvItem& x) { return x.n <= 32; });
+    int ns = 0;
+    max_small = 1;
+    for (auto& x : v)
+      if (x.n <= 32) { ++ns; max_small = std::max(max_small, x.n); }
+    return ns;
+  };
+  c->n_w_small = split(w, c->w_small_n);
+  c->n_dy_small = split(d, c->dy_small_n);
   CKS(upload(c, c->d_w_items, w));
   CKS(upload(c, c->d_dy_items, d));
   CKS(upload(c, c->d_hf_tab, tab));
@@ -860,8 +912,8 @@ extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P
     series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, z(1.0), 0, st);
   });
   run(c, "w_solve", flw, 1, st, [&] {
-    invert_blocks(INV_W, c->d_w_items, c->n_w_items, maxn, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw,
-                  nullptr, scr, c->d_status, st);
+    invert_blocks_split(INV_W, c->d_w_items, c->n_w_small, c->w_small_n, c->n_w_items, maxn, P0w, nullptr, nullptr, nullptr, 0.0,
+                        nullptr, nullptr, Pw, nullptr, scr, c->d_status, st);
   });
   run(c, "ft", flt, 1, st, [&] {
     series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, z(1.0), 0, st);
@@ -991,13 +1043,11 @@ static sgw_status self_energy_impl(sgw_ctx* c, const Z* G, const Z* Pt, const Z*
     const int ntc = t1 - t0;
     // X1[A][i][b] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
     run(c, t_vg.c_str(), P.fl_A_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, X1, G, P.d_A + (size_t)t0 * np, ni, c->d_ao_start,
-              c->d_ao_size, c->d_ao_doff, st);
+      bdm(c, 0, geom(1, naux * nao, nao, 0, 0, 0, 0, nao), V, X1, G, P.d_A + (size_t)t0 * np, ni, st);
     });
     // X2[A'][(i,b)] = sum_A P^q(tau)[A][A'] X1[A][(i,b)]
     run(c, t_pvg.c_str(), P.fl_B_t * ntc, 1, st, [&] {
-      bd_mult(geom(1, naux, nao * nao, 1, 1, 0, 0, naux), X1, X2, Pt, P.d_B + (size_t)t0 * np, ni, c->d_aux_start,
-              c->d_aux_size, c->d_aux_doff, st);
+      bdm(c, 1, geom(1, naux, nao * nao, 1, 1, 0, 0, naux), X1, X2, Pt, P.d_B + (size_t)t0 * np, ni, st);
     });
     const long long u0 = P.unit_start[t0], u1 = P.unit_start[t1];
     const long long ti0 = P.tile_start[t0], ti1 = P.tile_start[t1];
@@ -1206,8 +1256,8 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
       flg += 8.0 * Nk * naux * nao * (double)c->part_ao[w].elems;
     }
     run(c, "hf_k", flz, 1, st, [&] {
-      bd_mult(geom(1, naux * nao, nao, 0, 0, 0, 0, nao), c->d_V[1], Zw, gamma, c->plan_k.d_A + (size_t)w0 * Nk,
-              (long long)(w1 - w0) * Nk, c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+      bdm(c, 0, geom(1, naux * nao, nao, 0, 0, 0, 0, nao), (const double2*)c->d_V[1], Zw, (const double2*)gamma,
+          c->plan_k.d_A + (size_t)w0 * Nk, (long long)(w1 - w0) * Nk, st);
     });
     const long long u0 = c->plan_k_wbeg[g], u1 = c->plan_k_wbeg[g + 1];
     const long long t0 = c->plan_k_tbeg[g], t1 = c->plan_k_tbeg[g + 1];
@@ -1258,8 +1308,8 @@ static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const doubl
     for (int it = 0; it < 64; ++it) {
       run(c, "mu_search", 0.0, 1, st, [&] { mu_step(1, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
       run(c, "dyson_invert", fli, 1, st, [&] {
-        invert_blocks(INV_DYSON_TRACE, c->d_dy_items, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f, 0.0, s + 2, s + 3,
-                      nullptr, tpart, scr, c->d_status, st);
+        invert_blocks_split(INV_DYSON_TRACE, c->d_dy_items, c->n_dy_small, c->dy_small_n, c->n_dy_items, maxn, Sw, c->d_S, F,
+                            c->d_nu_f, 0.0, s + 2, s + 3, nullptr, tpart, scr, c->d_status, st);
       });
       run(c, "reduce", 0.0, 1, st, [&] { sum_partials(tpart, c->n_dy_items, d_sum, st); });
       run(c, "mu_search", 0.0, 1, st, [&] { mu_step(2, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
@@ -1267,8 +1317,8 @@ static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const doubl
     mu_dev = s + 2;
   }
   run(c, "dyson_invert", fli, 1, st, [&] {
-    invert_blocks(INV_DYSON_STORE, c->d_dy_items, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f, mu, mu_dev, nullptr,
-                  Gw, nullptr, scr, c->d_status, st);
+    invert_blocks_split(INV_DYSON_STORE, c->d_dy_items, c->n_dy_small, c->dy_small_n, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f,
+                        mu, mu_dev, nullptr, Gw, nullptr, scr, c->d_status, st);
   });
   run(c, "ft", 8.0 * nwf * (double)c->nt * ge, 1, st, [&] {
     series_map(c->d_TFbar, c->nt, nwf, Gw, ge, G_tau, ge, ge, z(1.0), 0, st);

@@ -146,6 +146,130 @@ void bd_mult(const BdGeom& g, const float2* X, float2* Y, const float2* M, const
 }
 
 // ---------------------------------------------------------------------------
+// Block-diagonal multiply, chunked.  A work unit is (row, block b, chunk of <= 8 outputs
+// inside b); the thread loads each element of its operand segment once and applies it to
+// all outputs of its chunk (8 multiply-adds per load), and the index arithmetic is paid
+// once per unit instead of once per output.
+//   right: Y[u][v][w0+l] = s * sum_j X[u][v][st+j] M[j][w0-st+l]          (unit over w)
+//   left : Y[u][v0+l][w] = s * sum_j M[v0-st+l][j] X[u][st+j][w]          (unit over v)
+// Units of partition p: ustart/ucnt/ubst/ubn/udoff[p * ustride + i], i < nunits[p].
+// ---------------------------------------------------------------------------
+constexpr int kChunk = 8;
+
+template <typename Z>
+__global__ void __launch_bounds__(256) k_bd_mult2(BdGeom g, const Z* __restrict__ X, Z* __restrict__ Y,
+                                                  const Z* __restrict__ M, const BdItem* __restrict__ items,
+                                                  long long nitems, const int* __restrict__ nunits,
+                                                  const int4* __restrict__ units, const long long* __restrict__ udoff,
+                                                  int ustride) {
+  for (long long it = blockIdx.y; it < nitems; it += gridDim.y) {
+    const BdItem item = items[it];
+    const int nu = nunits[item.part];
+    const int4* up = units + (long long)item.part * ustride;
+    const long long* dp = udoff + (long long)item.part * ustride;
+    const Z* Xb = X + item.x_off;
+    Z* Yb = Y + item.y_off;
+    const Z* Mb = M + item.m_off;
+    if (!g.left) {
+      // rows (u, v), units over w
+      const int rows = g.U * g.Vd;
+      const long long E = (long long)rows * nu;
+      for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / nu), ui = (int)(e - (long long)row * nu);
+        const int u = row / g.Vd, v = row - u * g.Vd;
+        const int4 un = up[ui];  // x: first output, y: count, z: block start, w: block size
+        const Z* Mblk = Mb + dp[ui];
+        const Z* xr = Xb + (long long)u * g.xs_u + (long long)v * g.xs_v + un.z;
+        const int lw0 = un.x - un.z;
+        Z acc[kChunk];
+#pragma unroll
+        for (int l = 0; l < kChunk; ++l) acc[l] = czero<Z>();
+        for (int j = 0; j < un.w; ++j) {
+          const Z x = xr[j];
+#pragma unroll
+          for (int l = 0; l < kChunk; ++l) {
+            if (l < un.y) {
+              Z m = g.trans ? Mblk[(long long)(lw0 + l) * un.w + j] : Mblk[(long long)j * un.w + lw0 + l];
+              if (g.conj) m.y = -m.y;
+              acc[l] = cfma(x, m, acc[l]);
+            }
+          }
+        }
+        Z* yr = Yb + (long long)u * g.ys_u + (long long)v * g.ys_v + un.x;
+        const Z sc = to_z(item.scale, acc[0]);
+#pragma unroll
+        for (int l = 0; l < kChunk; ++l)
+          if (l < un.y) {
+            Z r = cmul(sc, acc[l]);
+            if (g.accumulate) r = cadd(yr[l], r);
+            yr[l] = r;
+          }
+      }
+    } else {
+      // units over v, then w fastest (coalesced along w)
+      const long long E = (long long)g.U * nu * g.Wd;
+      for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(e % g.Wd);
+        const long long r = e / g.Wd;
+        const int ui = (int)(r % nu), u = (int)(r / nu);
+        const int4 un = up[ui];
+        const Z* Mblk = Mb + dp[ui];
+        const Z* xc = Xb + (long long)u * g.xs_u + (long long)un.z * g.xs_v + w;
+        const int lv0 = un.x - un.z;
+        Z acc[kChunk];
+#pragma unroll
+        for (int l = 0; l < kChunk; ++l) acc[l] = czero<Z>();
+        for (int j = 0; j < un.w; ++j) {
+          const Z x = xc[(long long)j * g.xs_v];
+#pragma unroll
+          for (int l = 0; l < kChunk; ++l) {
+            if (l < un.y) {
+              Z m = g.trans ? Mblk[(long long)j * un.w + lv0 + l] : Mblk[(long long)(lv0 + l) * un.w + j];
+              if (g.conj) m.y = -m.y;
+              acc[l] = cfma(m, x, acc[l]);
+            }
+          }
+        }
+        Z* yc = Yb + (long long)u * g.ys_u + (long long)un.x * g.ys_v + w;
+        const Z sc = to_z(item.scale, acc[0]);
+#pragma unroll
+        for (int l = 0; l < kChunk; ++l)
+          if (l < un.y) {
+            Z rr = cmul(sc, acc[l]);
+            if (g.accumulate) rr = cadd(yc[(long long)l * g.ys_v], rr);
+            yc[(long long)l * g.ys_v] = rr;
+          }
+      }
+    }
+  }
+}
+
+template <typename Z>
+static void bd_mult2_t(const BdGeom& g, const Z* X, Z* Y, const Z* M, const BdItem* items, long long nitems,
+                       const int* nunits, const int4* units, const long long* udoff, int ustride, int max_units,
+                       cudaStream_t st) {
+  if (nitems <= 0) return;
+  const long long E = g.left ? (long long)g.U * max_units * g.Wd : (long long)g.U * g.Vd * max_units;
+  unsigned bx = grid_for(E, 256, 4096);
+  long long by = 65535;
+  long long want = (8192 + bx - 1) / bx;
+  if (want < by) by = want;
+  if (by > nitems) by = nitems;
+  if (by < 1) by = 1;
+  k_bd_mult2<Z><<<dim3(bx, (unsigned)by), 256, 0, st>>>(g, X, Y, M, items, nitems, nunits, units, udoff, ustride);
+}
+void bd_mult2(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
+              const int* nunits, const int4* units, const long long* udoff, int ustride, int max_units,
+              cudaStream_t st) {
+  bd_mult2_t<double2>(g, X, Y, M, items, nitems, nunits, units, udoff, ustride, max_units, st);
+}
+void bd_mult2(const BdGeom& g, const float2* X, float2* Y, const float2* M, const BdItem* items, long long nitems,
+              const int* nunits, const int4* units, const long long* udoff, int ustride, int max_units,
+              cudaStream_t st) {
+  bd_mult2_t<float2>(g, X, Y, M, items, nitems, nunits, units, udoff, ustride, max_units, st);
+}
+
+// ---------------------------------------------------------------------------
 // Block Gram products with long K:  out[m][n] = alpha sum_r sum_k A_r[m][k] conj(B_r[n][k]).
 // Each unit covers one <= 32x32 tile of one output block and a range of
 // pairs r; it writes its partial sums, and gram_reduce adds the partials of
@@ -474,11 +598,147 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
       }
       if (tid == 0) {
         const double2 t = cmul(it.weight, make_double2(s_red[0], s_redi[0]));
-        tpart[itx] = make_double2(t.x, 0.0);
+        tpart[it.slot] = make_double2(t.x, 0.0);
       }
     }
     __syncthreads();
   }
+}
+
+// Warp-per-matrix variant for blocks of at most 32: lane i owns row i for the pivot search
+// and the elimination multipliers; all synchronisation is warp-level.
+constexpr int kWarpInvN = 32;
+__global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __restrict__ items, int nitems,
+                                                     const double2* __restrict__ Asrc, const double2* __restrict__ S,
+                                                     const double2* __restrict__ F, const double* __restrict__ nu,
+                                                     double mu_host, const double* __restrict__ mu_dev,
+                                                     const double* __restrict__ done_dev, double2* __restrict__ out,
+                                                     double2* __restrict__ tpart, int* __restrict__ status,
+                                                     int slot_n) {
+  // dynamic shared memory: 8 warp slots of slot_n x slot_n complex, then 8 x 32 pivot indices
+  extern __shared__ double2 smdyn[];
+  if (done_dev != nullptr && *done_dev != 0.0) return;
+  const double mu = mu_dev != nullptr ? *mu_dev : mu_host;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int itx = blockIdx.x * 8 + warp;
+  if (itx >= nitems) return;
+  const InvItem it = items[itx];
+  const int n = it.n, nn = n * n;
+  double2* A = smdyn + (long long)warp * slot_n * slot_n;
+  int* perm = reinterpret_cast<int*>(smdyn + 8LL * slot_n * slot_n) + warp * kWarpInvN;
+  for (int e = lane; e < nn; e += 32) {
+    const int i = e / n, j = e - i * n;
+    double2 a;
+    if (mode == INV_W) {
+      const double2 p = Asrc[it.a_off + e];
+      a = make_double2((i == j ? 1.0 : 0.0) - p.x, -p.y);
+    } else {
+      const double2 s = S[it.s_off + e], f = F[it.f_off + e], sg = Asrc[it.a_off + e];
+      const double w = nu[it.m];
+      a.x = mu * s.x - w * s.y - f.x - sg.x;
+      a.y = mu * s.y + w * s.x - f.y - sg.y;
+    }
+    A[e] = a;
+  }
+  __syncwarp();
+  for (int k = 0; k < n; ++k) {
+    double best = (lane >= k && lane < n) ? cabs2(A[lane * n + k]) : -1.0;
+    int bi = (lane >= k && lane < n) ? lane : n;
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const int p = __shfl_sync(0xffffffffu, bi, 0);
+    if (lane == 0) perm[k] = p;
+    if (p != k) {
+      for (int j = lane; j < n; j += 32) {
+        const double2 t = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = t;
+      }
+      __syncwarp();
+    }
+    double2 piv = A[k * n + k];
+    const double pm = cabs2(piv);
+    if (!(pm > 1e-300)) {
+      if (lane == 0) atomicExch(status, (int)DEV_SINGULAR);
+      piv = make_double2(1.0, 0.0);
+    }
+    const double2 inv = make_double2(piv.x / (pm > 1e-300 ? pm : 1.0), -piv.y / (pm > 1e-300 ? pm : 1.0));
+    const double2 colv = lane < n ? A[lane * n + k] : make_double2(0.0, 0.0);
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) A[k * n + j] = (j == k) ? inv : cmul(A[k * n + j], inv);
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {
+      const double2 ci = make_double2(__shfl_sync(0xffffffffu, colv.x, i), __shfl_sync(0xffffffffu, colv.y, i));
+      if (i == k) continue;
+      for (int j = lane; j < n; j += 32) {
+        if (j == k) {
+          const double2 t = cmul(ci, inv);
+          A[i * n + k] = make_double2(-t.x, -t.y);
+        } else {
+          const double2 t = cmul(ci, A[k * n + j]);
+          A[i * n + j] = make_double2(A[i * n + j].x - t.x, A[i * n + j].y - t.y);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k && lane < n) {
+      const double2 t = A[lane * n + k];
+      A[lane * n + k] = A[lane * n + p];
+      A[lane * n + p] = t;
+    }
+    __syncwarp();
+  }
+  if (mode == INV_W) {
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / n, j = e - i * n;
+      double2 a = A[e];
+      if (i == j) a.x -= 1.0;
+      out[it.out_off + e] = a;
+    }
+  } else if (mode == INV_DYSON_STORE) {
+    for (int e = lane; e < nn; e += 32) out[it.out_off + e] = A[e];
+  } else {
+    double2 s = make_double2(0.0, 0.0);
+    for (int e = lane; e < nn; e += 32) {
+      const int i = e / n, j = e - i * n;
+      s = cfma(A[e], S[it.s_off + j * n + i], s);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      s.x += __shfl_down_sync(0xffffffffu, s.x, off);
+      s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+    }
+    if (lane == 0) {
+      const double2 t = cmul(it.weight, s);
+      tpart[it.slot] = make_double2(t.x, 0.0);
+    }
+  }
+}
+
+void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_small_n, int nitems, int max_n,
+                         const double2* A, const double2* S, const double2* F, const double* nu, double mu,
+                         const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
+                         double2* scratch, int* status, cudaStream_t st) {
+  if (nsmall > 0) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(8 * kWarpInvN * kWarpInvN * sizeof(double2) + 8 * kWarpInvN * sizeof(int)));
+      attr = true;
+    }
+    const int sn = max_small_n < 1 ? 1 : max_small_n;
+    const size_t sm = (size_t)8 * sn * sn * sizeof(double2) + 8 * kWarpInvN * sizeof(int);
+    k_invert_warp<<<(nsmall + 7) / 8, 256, sm, st>>>(mode, items, nsmall, A, S, F, nu, mu, mu_dev, done_dev, out,
+                                                     trace_partial, status, sn);
+  }
+  if (nitems > nsmall)
+    invert_blocks(mode, items + nsmall, nitems - nsmall, max_n, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial,
+                  scratch, status, st);
 }
 
 void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,

@@ -68,6 +68,13 @@ void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, co
              const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st);
 void bd_mult(const BdGeom& g, const float2* X, float2* Y, const float2* M, const BdItem* items, long long nitems,
              const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st);
+// chunked variant (hot path): per partition a list of (first output, count <= 8, block start, block size)
+void bd_mult2(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
+              const int* nunits, const int4* units, const long long* udoff, int ustride, int max_units,
+              cudaStream_t st);
+void bd_mult2(const BdGeom& g, const float2* X, float2* Y, const float2* M, const BdItem* items, long long nitems,
+              const int* nunits, const int4* units, const long long* udoff, int ustride, int max_units,
+              cudaStream_t st);
 
 struct GramGeom {
   long long a_pair, b_pair;  // pair strides
@@ -97,12 +104,18 @@ struct InvItem {
   long long out_off; // destination block
   int n;
   int m;             // frequency index (Dyson)
+  int slot;          // trace partial slot (Dyson number mode)
   double2 weight;    // trace weight (Dyson number mode): partial = Re(weight * Tr[A^{-1} S])
 };
 enum InvMode { INV_W = 0, INV_DYSON_STORE = 1, INV_DYSON_TRACE = 2 };
 void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
                    const double2* F, const double* nu, double mu, const double* mu_dev, const double* done_dev,
                    double2* out, double2* trace_partial, double2* scratch, int* status, cudaStream_t st);
+// items [0, nsmall) have n <= 32 (one warp each), the rest run one CTA each
+void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_small_n, int nitems, int max_n,
+                         const double2* A, const double2* S, const double2* F, const double* nu, double mu,
+                         const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
+                         double2* scratch, int* status, cudaStream_t st);
 void mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi,
              cudaStream_t st);
 
@@ -186,6 +199,11 @@ struct sgw_ctx {
   std::vector<sgw::cplx> hostU[2];                // host copies, freed after upload
   int *d_ao_start = nullptr, *d_ao_size = nullptr, *d_aux_start = nullptr, *d_aux_size = nullptr;
   long long *d_ao_doff = nullptr, *d_aux_doff = nullptr;
+  // chunked unit tables of the orbital (0) and auxiliary (1) partitions, per wedge point
+  int* d_nunits[2] = {nullptr, nullptr};
+  int4* d_units[2] = {nullptr, nullptr};
+  long long* d_udoff[2] = {nullptr, nullptr};
+  int ustride[2] = {0, 0};
   int *d_full_start = nullptr, *d_full_size = nullptr;  // one block covering [0, max(nao,naux))
   long long* d_full_doff = nullptr;
   std::vector<int> pair_k1[2], pair_k2[2];
@@ -212,7 +230,7 @@ struct sgw_ctx {
   // static launch tables of the hot path (built once, so the iteration can be captured in a graph)
   bool tables = false;
   sgw::InvItem *d_w_items = nullptr, *d_dy_items = nullptr;
-  int n_w_items = 0, n_dy_items = 0;
+  int n_w_items = 0, n_dy_items = 0, n_w_small = 0, n_dy_small = 0, w_small_n = 1, dy_small_n = 1;
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
   // iteration buffers and the captured graph
   double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
