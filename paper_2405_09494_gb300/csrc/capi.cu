@@ -147,12 +147,23 @@ static void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
   c->prof_pending.push_back({id, a, b});
 }
 
-// Chunked block multiply over the orbital (kind 0) or auxiliary (kind 1) partitions.
-template <typename Z>
-static void bdm(sgw_ctx* c, int kind, const BdGeom& g, const Z* X, Z* Y, const Z* M, const BdItem* items,
-                long long nitems, cudaStream_t st) {
-  bd_mult2(g, X, Y, M, items, nitems, c->d_nunits[kind], c->d_units[kind], c->d_udoff[kind], c->ustride[kind],
-           c->ustride[kind], st);
+// Block multiply over the orbital (kind 0) or auxiliary (kind 1) partitions.  FP64 is bound by
+// the FP64 pipe and runs one output per thread (fewest registers, no predicated slots); FP32
+// uses the chunked variant where it reuses operands (right multiplies, large auxiliary blocks).
+static void bdm(sgw_ctx* c, int kind, const BdGeom& g, const double2* X, double2* Y, const double2* M,
+                const BdItem* items, long long nitems, cudaStream_t st) {
+  if (kind == 0)
+    bd_mult(g, X, Y, M, items, nitems, c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+  else
+    bd_mult(g, X, Y, M, items, nitems, c->d_aux_start, c->d_aux_size, c->d_aux_doff, st);
+}
+static void bdm(sgw_ctx* c, int kind, const BdGeom& g, const float2* X, float2* Y, const float2* M,
+                const BdItem* items, long long nitems, cudaStream_t st) {
+  if (kind == 0 && g.left)
+    bd_mult(g, X, Y, M, items, nitems, c->d_ao_start, c->d_ao_size, c->d_ao_doff, st);
+  else
+    bd_mult2(g, X, Y, M, items, nitems, c->d_nunits[kind], c->d_units[kind], c->d_udoff[kind], c->ustride[kind],
+             c->ustride[kind], st);
 }
 
 // Build the block-diagonal multiply geometry for a [U][Vd][Wd] contiguous tensor.

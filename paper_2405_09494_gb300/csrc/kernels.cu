@@ -115,7 +115,12 @@ __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__
           acc = cfma(Xp[j], m, acc);
         }
       }
-      acc = cmul(to_z(item.scale, acc), acc);
+      if (item.scale.y != 0.0 || (item.scale.x != 1.0 && item.scale.x != -1.0)) {
+        acc = cmul(to_z(item.scale, acc), acc);
+      } else if (item.scale.x == -1.0) {
+        acc.x = -acc.x;  // a sign flip, not a multiply
+        acc.y = -acc.y;
+      }
       Z* yp = Y + item.y_off + (long long)u * g.ys_u + (long long)v * g.ys_v + w;
       if (g.accumulate) acc = cadd(*yp, acc);
       *yp = acc;
@@ -605,8 +610,9 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
   }
 }
 
-// Warp-per-matrix variant for blocks of at most 32: lane i owns row i for the pivot search
-// and the elimination multipliers; all synchronisation is warp-level.
+// Warp-per-matrix variant for blocks of at most 32: lane i owns row i.  Each pivot step is
+// one warp-wide argmax, one row swap and one scaled-row broadcast; every lane then updates its
+// own row with independent multiply-adds (no serial chain over rows).
 constexpr int kWarpInvN = 32;
 __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __restrict__ items, int nitems,
                                                      const double2* __restrict__ Asrc, const double2* __restrict__ S,
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
                                                      const double* __restrict__ done_dev, double2* __restrict__ out,
                                                      double2* __restrict__ tpart, int* __restrict__ status,
                                                      int slot_n) {
-  // dynamic shared memory: 8 warp slots of slot_n x slot_n complex, then 8 x 32 pivot indices
+  // dynamic shared memory: 8 warp slots of slot_n rows x (slot_n + 1) complex (padded rows)
   extern __shared__ double2 smdyn[];
   if (done_dev != nullptr && *done_dev != 0.0) return;
   const double mu = mu_dev != nullptr ? *mu_dev : mu_host;
@@ -623,10 +629,9 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
   const int itx = blockIdx.x * 8 + warp;
   if (itx >= nitems) return;
   const InvItem it = items[itx];
-  const int n = it.n, nn = n * n;
-  double2* A = smdyn + (long long)warp * slot_n * slot_n;
-  int* perm = reinterpret_cast<int*>(smdyn + 8LL * slot_n * slot_n) + warp * kWarpInvN;
-  for (int e = lane; e < nn; e += 32) {
+  const int n = it.n, ld = slot_n + 1;
+  double2* A = smdyn + (long long)warp * slot_n * ld;
+  for (int e = lane; e < n * n; e += 32) {
     const int i = e / n, j = e - i * n;
     double2 a;
     if (mode == INV_W) {
@@ -638,11 +643,13 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
       a.x = mu * s.x - w * s.y - f.x - sg.x;
       a.y = mu * s.y + w * s.x - f.y - sg.y;
     }
-    A[e] = a;
+    A[i * ld + j] = a;
   }
   __syncwarp();
+  int myperm = lane;  // lane k records the row swapped into position k
+  double2* row = A + lane * ld;
   for (int k = 0; k < n; ++k) {
-    double best = (lane >= k && lane < n) ? cabs2(A[lane * n + k]) : -1.0;
+    double best = (lane >= k && lane < n) ? cabs2(row[k]) : -1.0;
     int bi = (lane >= k && lane < n) ? lane : n;
     for (int off = 16; off > 0; off >>= 1) {
       const double ob = __shfl_down_sync(0xffffffffu, best, off);
@@ -650,64 +657,65 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     const int p = __shfl_sync(0xffffffffu, bi, 0);
-    if (lane == 0) perm[k] = p;
-    if (p != k) {
-      for (int j = lane; j < n; j += 32) {
-        const double2 t = A[k * n + j];
-        A[k * n + j] = A[p * n + j];
-        A[p * n + j] = t;
-      }
-      __syncwarp();
+    if (lane == k) myperm = p;
+    if (p != k && lane < n) {  // lane j swaps column j of rows k and p
+      const double2 t = A[k * ld + lane];
+      A[k * ld + lane] = A[p * ld + lane];
+      A[p * ld + lane] = t;
     }
-    double2 piv = A[k * n + k];
+    __syncwarp();
+    double2 piv = A[k * ld + k];
     const double pm = cabs2(piv);
     if (!(pm > 1e-300)) {
       if (lane == 0) atomicExch(status, (int)DEV_SINGULAR);
       piv = make_double2(1.0, 0.0);
     }
-    const double2 inv = make_double2(piv.x / (pm > 1e-300 ? pm : 1.0), -piv.y / (pm > 1e-300 ? pm : 1.0));
-    const double2 colv = lane < n ? A[lane * n + k] : make_double2(0.0, 0.0);
+    const double den = pm > 1e-300 ? pm : 1.0;
+    const double2 inv = make_double2(piv.x / den, -piv.y / den);
+    const double2 c = lane < n ? row[k] : make_double2(0.0, 0.0);  // multiplier of my row
     __syncwarp();
-    for (int j = lane; j < n; j += 32) A[k * n + j] = (j == k) ? inv : cmul(A[k * n + j], inv);
+    if (lane < n) A[k * ld + lane] = (lane == k) ? inv : cmul(A[k * ld + lane], inv);  // scaled pivot row
     __syncwarp();
-    for (int i = 0; i < n; ++i) {
-      const double2 ci = make_double2(__shfl_sync(0xffffffffu, colv.x, i), __shfl_sync(0xffffffffu, colv.y, i));
-      if (i == k) continue;
-      for (int j = lane; j < n; j += 32) {
+    if (lane < n && lane != k) {
+      const double2* pr = A + k * ld;
+      for (int j = 0; j < n; ++j) {
         if (j == k) {
-          const double2 t = cmul(ci, inv);
-          A[i * n + k] = make_double2(-t.x, -t.y);
+          const double2 t = cmul(c, inv);
+          row[k] = make_double2(-t.x, -t.y);
         } else {
-          const double2 t = cmul(ci, A[k * n + j]);
-          A[i * n + j] = make_double2(A[i * n + j].x - t.x, A[i * n + j].y - t.y);
+          const double2 t = cmul(c, pr[j]);
+          row[j] = make_double2(row[j].x - t.x, row[j].y - t.y);
         }
       }
     }
     __syncwarp();
   }
   for (int k = n - 1; k >= 0; --k) {
-    const int p = perm[k];
+    const int p = __shfl_sync(0xffffffffu, myperm, k);
     if (p != k && lane < n) {
-      const double2 t = A[lane * n + k];
-      A[lane * n + k] = A[lane * n + p];
-      A[lane * n + p] = t;
+      const double2 t = row[k];
+      row[k] = row[p];
+      row[p] = t;
     }
-    __syncwarp();
   }
+  __syncwarp();
   if (mode == INV_W) {
-    for (int e = lane; e < nn; e += 32) {
+    for (int e = lane; e < n * n; e += 32) {
       const int i = e / n, j = e - i * n;
-      double2 a = A[e];
+      double2 a = A[i * ld + j];
       if (i == j) a.x -= 1.0;
       out[it.out_off + e] = a;
     }
   } else if (mode == INV_DYSON_STORE) {
-    for (int e = lane; e < nn; e += 32) out[it.out_off + e] = A[e];
+    for (int e = lane; e < n * n; e += 32) {
+      const int i = e / n, j = e - i * n;
+      out[it.out_off + e] = A[i * ld + j];
+    }
   } else {
     double2 s = make_double2(0.0, 0.0);
-    for (int e = lane; e < nn; e += 32) {
+    for (int e = lane; e < n * n; e += 32) {
       const int i = e / n, j = e - i * n;
-      s = cfma(A[e], S[it.s_off + j * n + i], s);
+      s = cfma(A[i * ld + j], S[it.s_off + j * n + i], s);
     }
     for (int off = 16; off > 0; off >>= 1) {
       s.x += __shfl_down_sync(0xffffffffu, s.x, off);
@@ -728,11 +736,11 @@ void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_sma
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(8 * kWarpInvN * kWarpInvN * sizeof(double2) + 8 * kWarpInvN * sizeof(int)));
+                           (int)(8 * kWarpInvN * (kWarpInvN + 1) * sizeof(double2)));
       attr = true;
     }
     const int sn = max_small_n < 1 ? 1 : max_small_n;
-    const size_t sm = (size_t)8 * sn * sn * sizeof(double2) + 8 * kWarpInvN * sizeof(int);
+    const size_t sm = (size_t)8 * sn * (sn + 1) * sizeof(double2);
     k_invert_warp<<<(nsmall + 7) / 8, 256, sm, st>>>(mode, items, nsmall, A, S, F, nu, mu, mu_dev, done_dev, out,
                                                      trace_partial, status, sn);
   }
