@@ -76,7 +76,23 @@ static inline unsigned grid_for(long long work, int threads, long long cap = 1 <
 // trans/conj select M^T / conj(M).  One thread per output element, looping
 // over exactly the elements of its block: no padding work for uneven blocks.
 // ---------------------------------------------------------------------------
-template <typename Z>
+// Sign flips as integer operations (no FP pipe slot).
+__device__ __forceinline__ double negd(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+__device__ __forceinline__ float negd(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
+// scale class by bit pattern: 0 = +1, 1 = -1, 2 = general
+__device__ __forceinline__ int scale_kind(double2 s) {
+  const long long xb = __double_as_longlong(s.x), yb = __double_as_longlong(s.y);
+  if ((yb & 0x7FFFFFFFFFFFFFFFLL) != 0) return 2;
+  if (xb == 0x3FF0000000000000LL) return 0;
+  if (xb == (long long)0xBFF0000000000000ULL) return 1;
+  return 2;
+}
+
+// LEFT/TRANS/CONJ are compile-time so the inner loop holds nothing but loads and the four
+// FMAs of a complex multiply-add (the FP64 pipe is the bound: no compare, negate or scale in it).
+template <typename Z, int LEFT, int TRANS, int CONJ>
 __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__ X, Z* __restrict__ Y,
                                                  const Z* __restrict__ M, const BdItem* __restrict__ items,
                                                  long long nitems, const int* __restrict__ ps,
@@ -85,6 +101,7 @@ __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__
   const int E = g.U * VW;
   for (long long it = blockIdx.y; it < nitems; it += gridDim.y) {
     const BdItem item = items[it];
+    const int sk = scale_kind(item.scale);
     const int* bs = ps + (long long)item.part * g.n_part;
     const int* bz = pz + (long long)item.part * g.n_part;
     const long long* bd = pd + (long long)item.part * g.n_part;
@@ -94,32 +111,34 @@ __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__
       const int v = r / g.Wd;
       const int w = r - v * g.Wd;
       Z acc = czero<Z>();
-      if (g.left) {
+      if (LEFT) {
         const int st = bs[v], n = bz[v];
         const Z* Mb = M + item.m_off + bd[v];
         const int lv = v - st;
         const Z* Xp = X + item.x_off + (long long)u * g.xs_u + w + (long long)st * g.xs_v;
+        const Z* mp = TRANS ? Mb + lv : Mb + (long long)lv * n;
+        const long long ms = TRANS ? n : 1;
         for (int j = 0; j < n; ++j) {
-          Z m = g.trans ? Mb[(long long)j * n + lv] : Mb[(long long)lv * n + j];
-          if (g.conj) m.y = -m.y;
-          acc = cfma(m, Xp[(long long)j * g.xs_v], acc);
+          const Z m = mp[j * ms];
+          acc = CONJ ? cfma_cj(Xp[(long long)j * g.xs_v], m, acc) : cfma(m, Xp[(long long)j * g.xs_v], acc);
         }
       } else {
         const int st = bs[w], n = bz[w];
         const Z* Mb = M + item.m_off + bd[w];
         const int lw = w - st;
         const Z* Xp = X + item.x_off + (long long)u * g.xs_u + (long long)v * g.xs_v + st;
+        const Z* mp = TRANS ? Mb + (long long)lw * n : Mb + lw;
+        const long long ms = TRANS ? 1 : n;
         for (int j = 0; j < n; ++j) {
-          Z m = g.trans ? Mb[(long long)lw * n + j] : Mb[(long long)j * n + lw];
-          if (g.conj) m.y = -m.y;
-          acc = cfma(Xp[j], m, acc);
+          const Z m = mp[j * ms];
+          acc = CONJ ? cfma_cj(Xp[j], m, acc) : cfma(Xp[j], m, acc);
         }
       }
-      if (item.scale.y != 0.0 || (item.scale.x != 1.0 && item.scale.x != -1.0)) {
+      if (sk == 1) {
+        acc.x = negd(acc.x);
+        acc.y = negd(acc.y);
+      } else if (sk == 2) {
         acc = cmul(to_z(item.scale, acc), acc);
-      } else if (item.scale.x == -1.0) {
-        acc.x = -acc.x;  // a sign flip, not a multiply
-        acc.y = -acc.y;
       }
       Z* yp = Y + item.y_off + (long long)u * g.ys_u + (long long)v * g.ys_v + w;
       if (g.accumulate) acc = cadd(*yp, acc);
@@ -139,7 +158,18 @@ static void bd_mult_t(const BdGeom& g, const Z* X, Z* Y, const Z* M, const BdIte
   if (want < by) by = want;
   if (by > nitems) by = nitems;
   if (by < 1) by = 1;
-  k_bd_mult<Z><<<dim3(bx, (unsigned)by), 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff);
+  const dim3 grid(bx, (unsigned)by);
+  const int key = (g.left ? 4 : 0) | (g.trans ? 2 : 0) | (g.conj ? 1 : 0);
+  switch (key) {
+    case 0: k_bd_mult<Z, 0, 0, 0><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 1: k_bd_mult<Z, 0, 0, 1><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 2: k_bd_mult<Z, 0, 1, 0><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 3: k_bd_mult<Z, 0, 1, 1><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 4: k_bd_mult<Z, 1, 0, 0><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 5: k_bd_mult<Z, 1, 0, 1><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    case 6: k_bd_mult<Z, 1, 1, 0><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+    default: k_bd_mult<Z, 1, 1, 1><<<grid, 256, 0, st>>>(g, X, Y, M, items, nitems, p_start, p_size, p_doff); break;
+  }
 }
 void bd_mult(const BdGeom& g, const double2* X, double2* Y, const double2* M, const BdItem* items, long long nitems,
              const int* p_start, const int* p_size, const long long* p_doff, cudaStream_t st) {
