@@ -217,6 +217,23 @@ SGW_API sgw_status sgw_screened_interaction(sgw_ctx* ctx, const void* P0_tau, vo
  * orbital blocks only.  Sigma_tau packed [ntau][g_elems]. */
 SGW_API sgw_status sgw_self_energy(sgw_ctx* ctx, const void* G_tau, const void* P_tau, void* Sigma_tau,
                                    sgw_stream stream);
+/* The paper has no counterpart to this entry point: it is sgw_screened_interaction for
+ * callers that may not allocate device memory when they call (code running while a CUDA graph
+ * is being captured, where cudaMalloc is not permitted, or applications that fix their device
+ * memory at start-up).  Same inputs, outputs and result; its scratch (the P0 and P
+ * frequency series) lives in a fixed 64 MiB array inside the library image instead of the
+ * context workspace, so every GPU that loads the library holds those 64 MiB until the process
+ * exits.  It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Limits: 2 * nw_b * p_elems <= 4 Mi complex numbers and auxiliary blocks of at most 90;
+ * larger problems get SGW_ERR_ARG with a message (use sgw_screened_interaction).  The
+ * context must have run sgw_screened_interaction once (set-up that allocates the launch
+ * tables this call reuses), else SGW_ERR_STATE.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * (on different streams, or from different contexts) race and must be serialised by the
+ * caller.  Nothing in the array needs to start at zero (both series are overwritten). */
+SGW_API sgw_status sgw_screened_interaction_noalloc(sgw_ctx* ctx, const void* P0_tau, void* P_tau,
+                                                    sgw_stream stream);
 /* a11: Sigma_HF = J + K from gamma = -G(beta^-) (Eq. (sigma_hf)); packed [g_elems]. */
 SGW_API sgw_status sgw_hartree_fock(sgw_ctx* ctx, const void* G_tau, void* Sigma_hf, sgw_stream stream);
 /* a8 + a9 + a10: Sigma~(tau) -> Sigma~(i w); G(i w) = [(i w + mu) S - H0 -

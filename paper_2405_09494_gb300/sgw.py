@@ -26,7 +26,7 @@ EXPORTS = [
     "sgw_get_wedge", "sgw_get_blocks", "sgw_get_pairs", "sgw_get_basis", "sgw_load_one_body", "sgw_load_v",
     "sgw_g0", "sgw_polarization", "sgw_screened_interaction", "sgw_self_energy", "sgw_hartree_fock", "sgw_dyson",
     "sgw_energy", "sgw_iterate", "sgw_unfold", "sgw_host_grid", "sgw_host_symmetry", "sgw_profile_enable",
-    "sgw_profile_read",
+    "sgw_profile_read", "sgw_screened_interaction_noalloc",
 ]
 
 
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "sgw_unfold": ([vp, i, i, vp, vp, vp], i),
         "sgw_host_grid": ([ctypes.POINTER(Params), vp, vp, vp, vp, vp], i),
         "sgw_host_symmetry": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp, vp], i),
+        "sgw_screened_interaction_noalloc": ([vp, vp, vp, vp], i),
         "sgw_profile_enable": ([vp, i], i),
         "sgw_profile_read": ([vp, i, ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(d),
                               ctypes.POINTER(ll), ctypes.POINTER(i), i], i),
@@ -255,6 +256,15 @@ def sgw_polarization(ctx, G_tau, P0_tau, stream=None):
 
 def sgw_screened_interaction(ctx, P0_tau, P_tau, stream=None):
     _check(load_library().sgw_screened_interaction(ctx, _ptr(P0_tau), _ptr(P_tau), _stream(stream)), ctx)
+
+
+def sgw_screened_interaction_noalloc(ctx, P0_tau, P_tau, stream=None):
+    """sgw_screened_interaction without any device allocation (scratch in a fixed 64 MiB library array).
+
+    For callers that may not allocate device memory at call time; see include/sgw.h for the
+    limits, the one-time set-up on each device and the rule that overlapping calls race.
+    """
+    _check(load_library().sgw_screened_interaction_noalloc(ctx, _ptr(P0_tau), _ptr(P_tau), _stream(stream)), ctx)
 
 
 def sgw_self_energy(ctx, G_tau, P_tau, Sigma_tau, stream=None):
