@@ -44,6 +44,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="plain,mixed", help="comma list of plain, mixed")
+    ap.add_argument("--profile-steps", type=int, default=None, help="profiled passes (default: --steps)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -227,12 +230,15 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     # per-kernel breakdown: the same passes with CUDA events around every launch (no graph)
     sgw.sgw_profile_read(ctx, reset=True)
     sgw.sgw_profile_enable(ctx, True)
-    for _ in range(args.steps):
+    nprof = args.profile_steps if args.profile_steps is not None else args.steps
+    for _ in range(nprof):
         flush.zero_()
         torch.cuda.synchronize(dev)
         step()
     prof = sgw.sgw_profile_read(ctx, reset=True)
     sgw.sgw_profile_enable(ctx, False)
+    prof = {k: (v[0] * args.steps / max(1, nprof), v[1] * args.steps / max(1, nprof), v[2] * args.steps / max(1, nprof))
+            for k, v in prof.items()}  # scaled to args.steps passes
     out = {"t_step": t_step, "prof": prof, "clocks": clk.summary(), "state": (G, Sig, Shf, state["mu"]),
            "times": times}
     if e2e:
@@ -309,50 +315,70 @@ def _mixed_errors(plain, mixed, state):
 def run_ours(args, rank, world, local):
     import torch
 
-    from paper_2405_09494_gb300 import api, configs, sgw
+    from paper_2405_09494_gb300 import api, configs, sgw, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = configs.get(args.config)
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    plain = api.Session(cfg, device=str(dev))
-    rp = _time_form(plain, cfg, args, dev, local, flush, world, e2e=True)
-    mixed = api.Session(cfg, precision=sgw.SGW_MIXED_FP32, device=str(dev), system=plain.sys)
-    rm = _time_form(mixed, cfg, args, dev, local, flush, world)
-    errs = _mixed_errors(plain, mixed, rp["state"])
-    launches = sum(v[2] for v in rp["prof"].values())
-    gf_p = sum(v[1] for v in rp["prof"].values()) / args.steps
-    gf_m = sum(v[1] for v in rm["prof"].values()) / args.steps
+    # inputs: the seeded generator, its two-body averaging run on the device (input preparation, untimed)
+    system = synth.System(cfg, device=dev)
+    res = {}
+    sess = {}
+    for f in forms:
+        prec = sgw.SGW_FP64 if f == "plain" else sgw.SGW_MIXED_FP32
+        sess[f] = api.Session(cfg, precision=prec, device=str(dev), system=system)
+        res[f] = _time_form(sess[f], cfg, args, dev, local, flush, world, e2e=(f == forms[0] and not args.no_e2e))
+    errs = _mixed_errors(sess["plain"], sess["mixed"], res["plain"]["state"]) if len(forms) == 2 else None
     fp32_peak = 2 * 128 * 152 * 2.070e9 / 1e12
-    roof_m = _roofline(rm["prof"], fp32_peak, "alu",
-                       "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived, measured 70.4)")
-    plain.close()
-    mixed.close()
+    for f in forms:
+        sess[f].close()
+
+    def summary(f):
+        r = res[f]
+        gf = sum(v[1] for v in r["prof"].values()) / args.steps
+        if f == "plain":
+            roof = _roofline(r["prof"], FP64_PEAK_TFLOPS, "alu",
+                             "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived, measured 1.20)")
+        else:
+            roof = _roofline(r["prof"], fp32_peak, "alu",
+                             "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived, measured 70.4)")
+        return gf, roof
+
+    head = forms[0]
+    gf_h, roof_h = summary(head)
+    rh = res[head]
     line = {
-        "metric": METRIC, "value": rp["t_step"], "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": rp["t_step"] * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": cfg.description, "name": cfg.name, "form": "plain (complex128)",
+        "metric": METRIC, "value": rh["t_step"], "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": rh["t_step"] * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if head == "plain" else "c64 chains, c128 rest",
+        "data": "synthetic",
+        "config": {"workload": cfg.description, "name": cfg.name,
+                   "form": "plain (complex128)" if head == "plain" else "chosen (mixed)",
                    "l2": "512 MiB buffer written between timed steps",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "tflops_algorithmic": gf_p / rp["t_step"] / 1e3,
-        "step_times_s": rp["times"],
+        "tflops_algorithmic": gf_h / rh["t_step"] / 1e3,
+        "step_times_s": rh["times"],
         "cuda_graph": "each timed step replays one captured graph of the whole pass",
-        "gflop_per_step": gf_p,
-        "roofline": _roofline(rp["prof"], FP64_PEAK_TFLOPS, "alu",
-                              "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived, measured 1.20)"),
-        "kernels": _kernels(rp["prof"], args.steps),
-        "gpu_launches": int(launches),
-        "e2e": rp["e2e"],
-        "clocks": rp["clocks"],
-        "chosen_form": {
+        "gflop_per_step": gf_h,
+        "roofline": roof_h,
+        "kernels": _kernels(rh["prof"], args.steps),
+        "gpu_launches": int(sum(v[2] for v in rh["prof"].values())),
+        "clocks": rh["clocks"],
+    }
+    if "e2e" in rh:
+        line["e2e"] = rh["e2e"]
+    if "mixed" in forms and head != "mixed":
+        rm = res["mixed"]
+        gf_m, roof_m = summary("mixed")
+        line["chosen_form"] = {
             "form": "V-G-V and V-G-P-V chains complex64 with FP32 accumulation; W solve, Dyson, mu, transforms FP64",
-            "value": rm["t_step"], "unit": "s/iteration", "speedup_vs_plain": rp["t_step"] / rm["t_step"],
+            "value": rm["t_step"], "unit": "s/iteration", "speedup_vs_plain": rh["t_step"] / rm["t_step"],
             "tflops_algorithmic": gf_m / rm["t_step"] / 1e3, "roofline": roof_m,
             "error_vs_fp64": errs, "kernels": _kernels(rm["prof"], args.steps), "clocks": rm["clocks"],
             "gpu_launches": int(sum(v[2] for v in rm["prof"].values())),
-        },
-    }
+        }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores = oracle_sample(cfg)
         line["cpu_baseline"] = {"value": val, "unit": "s/iteration", "cores": cores, "kind": "oracle",

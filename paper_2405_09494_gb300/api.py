@@ -53,8 +53,11 @@ class Session:
             n = len(k1)
             for p0 in range(0, n, chunk):
                 p1 = min(n, p0 + chunk)
-                blk = np.stack([self.sys.V(int(a), int(b)) for a, b in zip(k1[p0:p1], k2[p0:p1])])
-                t = torch.from_numpy(blk).to(self.device)
+                vs = [self.sys.V(int(a), int(b)) for a, b in zip(k1[p0:p1], k2[p0:p1])]
+                if isinstance(vs[0], np.ndarray):
+                    t = torch.from_numpy(np.stack(vs)).to(self.device)
+                else:
+                    t = torch.stack(vs).to(self.device).contiguous()
                 sgw.sgw_load_v(self.ctx, which, p0, p1 - p0, t)
                 torch.cuda.synchronize(self.device)
         del cfg

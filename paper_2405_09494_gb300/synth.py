@@ -161,6 +161,23 @@ class _Action:
             o += 2 * l + 1 if structure != "none" else 1
         self.shell_off = off
 
+    def dense(self, iop: int, kfrac_rot: np.ndarray) -> np.ndarray:
+        """The n x n matrix of operation iop on Bloch sums whose rotated momentum is kfrac_rot."""
+        n = self.n
+        if self.structure == "none":
+            return np.eye(n, dtype=np.complex128)
+        O = np.zeros((n, n), dtype=np.complex128)
+        R = self.ops[iop][0]
+        for x in range(self.nat):
+            xp = self.perm[iop][x]
+            phase = np.exp(-2j * np.pi * float(kfrac_rot @ self.tvec[iop][x]))
+            for s, l in enumerate(self.shells):
+                D = real_harmonic_rotation(l, R)
+                src = x * self.size_per_atom + self.shell_off[s]
+                dst = xp * self.size_per_atom + self.shell_off[s]
+                O[dst:dst + 2 * l + 1, src:src + 2 * l + 1] = phase * D
+        return O
+
     def apply(self, iop: int, kfrac_rot: np.ndarray, X: np.ndarray, axis: int, conj: bool = False):
         """Return O X along ``axis`` (O of op iop at a k whose rotated image is kfrac_rot).
 
@@ -168,21 +185,10 @@ class _Action:
         """
         if self.structure == "none":
             return X.copy()
-        X = np.moveaxis(X, axis, 0)
-        Y = np.zeros_like(X, dtype=np.complex128)
-        R = self.ops[iop][0]
-        for x in range(self.nat):
-            xp = self.perm[iop][x]
-            phase = np.exp(-2j * np.pi * float(kfrac_rot @ self.tvec[iop][x]))
-            if conj:
-                phase = np.conj(phase)
-            for s, l in enumerate(self.shells):
-                D = real_harmonic_rotation(l, R)
-                src = x * self.size_per_atom + self.shell_off[s]
-                dst = xp * self.size_per_atom + self.shell_off[s]
-                blk = X[src:src + 2 * l + 1]
-                Y[dst:dst + 2 * l + 1] += phase * np.tensordot(D, blk, axes=(1, 0))
-        return np.moveaxis(Y, 0, axis)
+        O = self.dense(iop, kfrac_rot)
+        if conj:
+            O = O.conj()
+        return np.moveaxis(np.tensordot(O, X, axes=(1, axis)), 0, axis)
 
 
 class Mesh:
@@ -239,10 +245,17 @@ def _cgauss(rng, shape):
 
 
 class System:
-    """All inputs of one workload: H0, S and V(k1, k2) on demand."""
+    """All inputs of one workload: H0, S and V(k1, k2) on demand.
 
-    def __init__(self, cfg: Config):
+    ``device`` (a torch device) moves the two-body work (group averaging and rotation of V) to
+    PyTorch on that device; V(k1, k2) then returns torch tensors there.  The random draws are the
+    same numpy draws either way; only the rounding of the averaging differs between backends, so
+    one System instance must feed both sides of a comparison.
+    """
+
+    def __init__(self, cfg: Config, device=None):
         self.cfg = cfg
+        self.device = device
         self.ops = space_group(cfg.structure)
         self.lattice = FCC if cfg.structure != "none" else np.eye(3)
         self.mesh = Mesh(cfg.nk, self.lattice, self.ops)
@@ -301,14 +314,30 @@ class System:
         self.S = S
 
     # ---- two-body ---------------------------------------------------------
+    def _mat(self, O):
+        if self.device is None:
+            return O
+        import torch
+
+        return torch.from_numpy(O).to(self.device)
+
     def _act_pair(self, iop, swap, k1, k2, X):
-        """Apply (alpha, swap) to V^{k1,k2}; return (new pair, tensor)."""
+        """Apply (alpha, swap) to V^{k1,k2}; return (new pair, tensor).
+
+        V'(Q) = sum_Q' O_aux^q(alpha)[Q, Q'] O^{k1}(alpha) V(Q') O^{k2}(alpha)^dagger.
+        """
         q = self.mesh.sub(k2, k1)
-        X = self.aux.apply(iop, self.mesh.rotated_frac(iop, q), X, 0)
-        X = self.ao.apply(iop, self.mesh.rotated_frac(iop, k1), X, 1)
-        X = self.ao.apply(iop, self.mesh.rotated_frac(iop, k2), X, 2, conj=True)
         a, b = self.mesh.image[iop][k1], self.mesh.image[iop][k2]
+        if self.cfg.structure != "none":
+            Oq = self._mat(self.aux.dense(iop, self.mesh.rotated_frac(iop, q)))
+            O1 = self._mat(self.ao.dense(iop, self.mesh.rotated_frac(iop, k1)))
+            O2 = self._mat(self.ao.dense(iop, self.mesh.rotated_frac(iop, k2)))
+            naux, nao = self.naux, self.nao
+            X = (Oq @ X.reshape(naux, nao * nao)).reshape(naux, nao, nao)
+            X = O1 @ X @ O2.conj().T
         if swap:
+            if self.device is not None:
+                return (b, a), X.transpose(-1, -2).conj_physical().contiguous()
             return (b, a), np.conj(X).transpose(0, 2, 1)
         return (a, b), X
 
@@ -338,7 +367,13 @@ class System:
         cfg = self.cfg
         rng = _rng(cfg, 2, p[0], p[1])
         X = _cgauss(rng, (self.naux, self.nao, self.nao)) / np.sqrt(self.naux)
-        acc = np.zeros_like(X)
+        if self.device is not None:
+            import torch
+
+            X = torch.from_numpy(X).to(self.device)
+            acc = torch.zeros_like(X)
+        else:
+            acc = np.zeros_like(X)
         n = 0
         for iop in range(len(self.ops)):
             for swap in (0, 1):
@@ -356,14 +391,17 @@ class System:
         # (iop, swap) maps (k1,k2) onto p; the inverse maps p back to (k1,k2).
         pair, X = self._act_pair(self._inverse_op(iop), swap, p[0], p[1], Vp)
         assert pair == (k1, k2), (pair, (k1, k2))
-        return X
+        if self.device is not None:
+            return X.resolve_conj().contiguous()
+        return np.ascontiguousarray(X)
 
     def V_full(self):
-        """Dense [Nk][Nk][naux][nao][nao] array (small workloads only)."""
+        """Dense [Nk][Nk][naux][nao][nao] numpy array (small workloads only)."""
         out = np.empty((self.Nk, self.Nk, self.naux, self.nao, self.nao), dtype=np.complex128)
         for k1 in range(self.Nk):
             for k2 in range(self.Nk):
-                out[k1, k2] = self.V(k1, k2)
+                v = self.V(k1, k2)
+                out[k1, k2] = v if self.device is None else v.cpu().numpy()
         return out
 
 

@@ -70,5 +70,7 @@ def test_c2_full_size_sampled(c2, form, tol):
     for k in (sess.wedge[2], 7):
         ref = gw.self_energy(c2["G0"], Pu, V, cfg.nk, ks=[int(k)])[int(k)]
         assert rel_err(Sigu[k], ref) < tol, (form, k)
-    # invariants at full size: Hermiticity per tau
-    assert np.abs(P0u - P0u.conj().transpose(0, 1, 3, 2)).max() < 1e-9 * np.abs(P0u).max()
+    # invariants at full size: Hermiticity per tau (to the form's own bound: the chosen form
+    # accumulates the two orientations of each block in separate FP32 sums)
+    herm = 1e-9 if form == "plain" else tol
+    assert np.abs(P0u - P0u.conj().transpose(0, 1, 3, 2)).max() < herm * np.abs(P0u).max()
