@@ -10,18 +10,6 @@
 
 using namespace sgw;
 
-#define CK(call)                                                                               \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-#define CKS(expr)                      \
-  do {                                 \
-    sgw_status s_ = (expr);            \
-    if (s_ != SGW_OK) return s_;       \
-  } while (0)
-
 namespace {
 
 template <typename T>
@@ -117,35 +105,6 @@ static sgw_status need_built(sgw_ctx* c) {
 }
 
 static long long vsize(const sgw_ctx* c) { return (long long)c->naux * c->nao * c->nao; }
-
-// Launch through the accounting: kernel class `name`, algorithmic flops, number of kernels.
-template <class F>
-static void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStream_t st, F&& f) {
-  int id = -1;
-  for (size_t i = 0; i < c->prof_names.size(); ++i)
-    if (c->prof_names[i] == name) { id = (int)i; break; }
-  if (id < 0) {
-    id = (int)c->prof_names.size();
-    c->prof_names.push_back(name);
-    c->prof_ms.push_back(0.0);
-    c->prof_flops.push_back(0.0);
-    c->prof_launch.push_back(0);
-  }
-  c->prof_flops[id] += flops;
-  c->prof_launch[id] += nkern;
-  c->launches += nkern;
-  if (!c->prof_on) {
-    f();
-    return;
-  }
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  cudaEventRecord(a, st);
-  f();
-  cudaEventRecord(b, st);
-  c->prof_pending.push_back({id, a, b});
-}
 
 // Block multiply over the orbital (kind 0) or auxiliary (kind 1) partitions.  FP64 is bound by
 // the FP64 pipe and runs one output per thread (fewest registers, no predicated slots); FP32
@@ -329,6 +288,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_aux_start); dfree(c->d_aux_size); dfree(c->d_aux_doff);
   dfree(c->d_full_start); dfree(c->d_full_size); dfree(c->d_full_doff);
   for (int b = 0; b < 2; ++b) { dfree(c->d_nunits[b]); dfree(c->d_units[b]); dfree(c->d_udoff[b]); }
+  tc_free(c);
   dfree(c->d_V[0]); dfree(c->d_V[1]); dfree(c->d_V32[0]); dfree(c->d_V32[1]); dfree(c->d_H0); dfree(c->d_S);
   dfree(c->d_el_boff); dfree(c->d_el_eoff); dfree(c->d_el_bn); dfree(c->d_el_i); dfree(c->d_el_j); dfree(c->d_el_w);
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
@@ -351,6 +311,10 @@ extern "C" SGW_API sgw_status sgw_sync(sgw_ctx* c, sgw_stream stream) {
   if (st == DEV_SINGULAR) {
     cudaMemset(c->d_status, 0, sizeof(int));
     return c->fail(SGW_ERR_SINGULAR, "zero pivot in a block inversion");
+  }
+  if (st == DEV_TIMEOUT) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    return c->fail(SGW_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of time; its results are invalid");
   }
   return SGW_OK;
 }
@@ -468,6 +432,8 @@ extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_struct
       cudaMalloc(&c->d_S, c->g_elems * sizeof(double2)) != cudaSuccess)
     return c->fail(SGW_ERR_OOM, "allocating one-body blocks");
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
+  tc_free(c);
+  c->use_tc = tc_supported(c);
   c->built = true;
   out->nkpts = Nk;
   out->nwedge = nw;
@@ -635,7 +601,12 @@ extern "C" SGW_API sgw_status sgw_load_v(sgw_ctx* c, int which, long long first,
     });
     if (c->p.precision == SGW_MIXED_FP32) {
       const long long pbeg = first + p0;
-      run(c, "convert", 0.0, 1, st, [&] { to_c64(c->d_V[which] + pbeg * vs, c->d_V32[which] + pbeg * vs, np_ * vs, st); });
+      run(c, "convert", 0.0, 1, st, [&] {
+        if (c->use_tc)
+          tc_store_v(c, which, c->d_V[which] + pbeg * vs, c->d_V32[which] + pbeg * vs, np_, st);
+        else
+          to_c64(c->d_V[which] + pbeg * vs, c->d_V32[which] + pbeg * vs, np_ * vs, st);
+      });
     }
     CK(cudaStreamSynchronize(st));
     for (long long i = 0; i < np_; ++i) c->v_loaded[which][first + p0 + i] = 1;
@@ -821,10 +792,13 @@ extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, vo
   CKS(need_built(c));
   if (!c->have_v[0]) return c->fail(SGW_ERR_STATE, "polarization pairs of V not loaded");
   if (!G_tau || !P0_tau) return SGW_ERR_ARG;
-  CKS(build_p0_plan(c));
+  if (!c->use_tc) CKS(build_p0_plan(c));
   cudaStream_t st = S(stream);
   double2* out = static_cast<double2*>(P0_tau);
-  if (c->p.precision == SGW_MIXED_FP32) {
+  if (c->use_tc) {
+    // tensor-core chains: TF32 head/tail products, FP32 accumulation, FP64 sums of the partial tiles
+    CKS(tc_polarization(c, static_cast<const double2*>(G_tau), out, st));
+  } else if (c->p.precision == SGW_MIXED_FP32) {
     // G(tau) rounded to complex64 once; the chains accumulate in FP32, P0 is returned in FP64
     CKS(ensure_g32(c, (size_t)c->nt * c->g_elems));
     run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)c->nt * c->g_elems, st); });
@@ -1075,10 +1049,12 @@ extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, con
   CKS(need_built(c));
   if (!c->have_v[1]) return c->fail(SGW_ERR_STATE, "self-energy pairs of V not loaded");
   if (!G_tau || !P_tau || !Sigma_tau) return SGW_ERR_ARG;
-  CKS(build_sigma_plan(c));
+  if (!c->use_tc) CKS(build_sigma_plan(c));
   cudaStream_t st = S(stream);
   double2* out = static_cast<double2*>(Sigma_tau);
-  if (c->p.precision == SGW_MIXED_FP32) {
+  if (c->use_tc) {
+    CKS(tc_self_energy(c, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau), out, st));
+  } else if (c->p.precision == SGW_MIXED_FP32) {
     const size_t gn = (size_t)c->nt * c->g_elems, pn = (size_t)c->nt * c->p_elems;
     CKS(ensure_g32(c, gn + pn));
     run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)gn, st); });

@@ -15,7 +15,7 @@ namespace sgw {
 using cplx = std::complex<double>;
 
 // Status codes written by kernels into the context's device status word.
-enum DeviceStatus : int { DEV_OK = 0, DEV_SINGULAR = 1 };
+enum DeviceStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2 };
 
 // One block-diagonal partition of an index range [0, n): for every index v,
 // the first index and size of its block and the offset of the block's data
@@ -154,6 +154,7 @@ double mu_bisect_device(const double* eps, const double* wts, int n, double beta
 }  // namespace sgw
 
 namespace sgw {
+struct TcPlan;  // tensor-core jobs of the chosen form (tc.cu)
 // Cached launch tables of one contraction (P0, Sigma or exchange), built once.
 struct ContractionPlan {
   bool built = false;
@@ -210,7 +211,10 @@ struct sgw_ctx {
 
   // inputs in block coordinates
   double2 *d_V[2] = {nullptr, nullptr};  // [npairs][naux][nao][nao]
-  float2* d_V32[2] = {nullptr, nullptr};  // complex64 copies for the chosen form
+  float2* d_V32[2] = {nullptr, nullptr};  // complex64 copies for the chosen form (orientation 1 as
+                                          // [pair][i][A][a] when the tensor-core chains are used)
+  bool use_tc = false;                     // chosen form runs its chains on the tensor cores
+  sgw::TcPlan* tc = nullptr;
   float2* d_g32 = nullptr;                 // complex64 tau series (chosen form)
   size_t g32_elems = 0;
   double2 *d_H0 = nullptr, *d_S = nullptr;  // packed [g_elems]
@@ -265,6 +269,57 @@ struct sgw_ctx {
     return s;
   }
 };
+
+// Launch through the accounting: kernel class `name`, algorithmic flops, number of kernels; with
+// profiling on, CUDA events on the launching stream bracket the launches.
+namespace sgw {
+template <class F>
+inline void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStream_t st, F&& f) {
+  int id = -1;
+  for (size_t i = 0; i < c->prof_names.size(); ++i)
+    if (c->prof_names[i] == name) { id = (int)i; break; }
+  if (id < 0) {
+    id = (int)c->prof_names.size();
+    c->prof_names.push_back(name);
+    c->prof_ms.push_back(0.0);
+    c->prof_flops.push_back(0.0);
+    c->prof_launch.push_back(0);
+  }
+  c->prof_flops[id] += flops;
+  c->prof_launch[id] += nkern;
+  c->launches += nkern;
+  if (!c->prof_on) {
+    f();
+    return;
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  c->prof_pending.push_back({id, a, b});
+}
+
+// tensor-core chains of the chosen form (tc.cu)
+bool tc_supported(const sgw_ctx* c);
+void tc_free(sgw_ctx* c);
+void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long long npairs, cudaStream_t st);
+sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStream_t st);
+sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, cudaStream_t st);
+}  // namespace sgw
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKS(expr)                      \
+  do {                                 \
+    sgw_status s_ = (expr);            \
+    if (s_ != SGW_OK) return s_;       \
+  } while (0)
 
 // set-up helpers (setup.cpp)
 namespace sgw {
