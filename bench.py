@@ -34,6 +34,10 @@ if ROOT not in sys.path:
 
 METRIC = "scGW iteration time (s) and TFLOP/s vs tensor peak, mixed vs FP64 at stated error"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz
+# TF32 tensor peak from the measured bf16 burst (MEASURED_PEAKS.json) and the nominal 1.1 / 2.25 ratio;
+# the chosen form spends three TF32 products per FP32-accurate product
+TF32_X3_PEAK_TFLOPS = 1907.2 * 1.1 / 2.25 / 3
+FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 
 
 def _args():
@@ -47,6 +51,8 @@ def _args():
     ap.add_argument("--forms", default="plain,mixed", help="comma list of plain, mixed")
     ap.add_argument("--profile-steps", type=int, default=None, help="profiled passes (default: --steps)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check-errors", action="store_true",
+                    help="with --forms mixed: one FP64 pass from the chosen form's state for its error")
     return ap.parse_args()
 
 
@@ -270,11 +276,22 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     return out
 
 
-def _roofline(prof, peak, bound, note):
+def _roofline(prof):
+    """Roofline of the kernel class with the most device time, against the peak of the pipe it runs on."""
     compute = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(compute, key=lambda k: compute[k][0])
     ms, gf, nl = compute[dom]
     achieved = (gf / nl) / (ms / nl)  # GFLOP per launch / ms per launch = TFLOP/s
+    if dom.endswith("_tc"):
+        bound, peak, note = "tensor", TF32_X3_PEAK_TFLOPS, (
+            "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 burst 1907.2 TF/s "
+            "x nominal TF32/BF16 ratio 1.1/2.25 = 932 TF/s, / 3 = 311 TF/s (of measured)")
+    elif dom.endswith("_f32"):
+        bound, peak, note = "alu", FP32_PEAK_TFLOPS, (
+            "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived; a probe measured 70.4)")
+    else:
+        bound, peak, note = "alu", FP64_PEAK_TFLOPS, (
+            "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived; a DFMA probe measured 1.20)")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "peak_note": note}
 
@@ -330,21 +347,21 @@ def run_ours(args, rank, world, local):
         prec = sgw.SGW_FP64 if f == "plain" else sgw.SGW_MIXED_FP32
         sess[f] = api.Session(cfg, precision=prec, device=str(dev), system=system)
         res[f] = _time_form(sess[f], cfg, args, dev, local, flush, world, e2e=(f == forms[0] and not args.no_e2e))
-    errs = _mixed_errors(sess["plain"], sess["mixed"], res["plain"]["state"]) if len(forms) == 2 else None
-    fp32_peak = 2 * 128 * 152 * 2.070e9 / 1e12
+    if len(forms) == 2:
+        errs = _mixed_errors(sess["plain"], sess["mixed"], res["plain"]["state"])
+    elif forms == ["mixed"] and args.check_errors:
+        ref = api.Session(cfg, precision=sgw.SGW_FP64, device=str(dev), system=system)
+        errs = _mixed_errors(ref, sess["mixed"], res["mixed"]["state"])
+        ref.close()
+    else:
+        errs = None
     for f in forms:
         sess[f].close()
 
     def summary(f):
         r = res[f]
         gf = sum(v[1] for v in r["prof"].values()) / args.steps
-        if f == "plain":
-            roof = _roofline(r["prof"], FP64_PEAK_TFLOPS, "alu",
-                             "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived, measured 1.20)")
-        else:
-            roof = _roofline(r["prof"], fp32_peak, "alu",
-                             "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived, measured 70.4)")
-        return gf, roof
+        return gf, _roofline(r["prof"])
 
     head = forms[0]
     gf_h, roof_h = summary(head)
@@ -369,6 +386,8 @@ def run_ours(args, rank, world, local):
     }
     if "e2e" in rh:
         line["e2e"] = rh["e2e"]
+    if head == "mixed" and errs is not None:
+        line["error_vs_fp64"] = errs
     if "mixed" in forms and head != "mixed":
         rm = res["mixed"]
         gf_m, roof_m = summary("mixed")

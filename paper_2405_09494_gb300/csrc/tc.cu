@@ -26,6 +26,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "sgw_internal.h"
@@ -36,16 +38,19 @@ namespace sgw {
 
 // One job: an A slab range and a B operand; the CTA picks its 128-row tile of the job by blockIdx.
 struct alignas(16) TcJob {
-  int a_y, a_z, b_y, b_z;  // first row and slab of the A and B boxes
-  int a_x, b_x;            // first contracted coordinate (reals, multiple of 4)
-  int nslab, nchunk;       // contraction loop: nslab slabs x nchunk chunks of 16 reals
-  int a_dz, b_dz;          // slab increments
-  int m_rows;              // rows of A the job covers (tiles of 128)
-  int n_valid, n_mma;      // stored columns; MMA width (multiple of 16, <= 128)
-  int pad;
-  long long out_off;       // partial slot (Gram) or output base (affine store)
+  int a_y = 0, a_z = 0, b_y = 0, b_z = 0;  // first row and slab of the A and B boxes
+  int a_x = 0, b_x = 0;    // first contracted coordinate (reals, multiple of 4)
+  int nslab = 1, nchunk = 1;  // contraction loop: nslab slabs x nchunk chunks of 16 reals
+  int a_dz = 0, b_dz = 0;  // slab increments
+  int m_rows = 0;          // rows of A the job covers (tiles of 128)
+  int n_valid = 0, n_mma = 16;  // stored columns; MMA width (multiple of 16, <= 128)
+  // row groups (tau stacking): g_count groups of g_rows tile rows, group g read from slab
+  // a_z + g g_dz, g_valid rows of each stored; g_count = 1: one group of m_rows rows
+  int g_count = 1, g_rows = 0, g_valid = 0, g_dz = 0;
+  int pad0 = 0, pad1 = 0, pad2 = 0;
+  long long out_off = 0;   // partial slot (Gram) or output base (affine store)
 };
-static_assert(sizeof(TcJob) == 64, "TcJob layout");
+static_assert(sizeof(TcJob) == 96, "TcJob layout");
 
 // Output tile of a Gram reduction over the partial tiles of its units (FP64 sum in order).
 struct alignas(16) TcTile {
@@ -55,6 +60,7 @@ struct alignas(16) TcTile {
 
 struct TcArgs {
   int mtiles;          // 128-row tiles per job
+  int a_box;           // rows per A box of the A tensor map (8 or 32)
   int mode;            // 0: FP32 partial tile [n][m] at out_off; 1: affine store
   long long Rs, S1, S2;  // affine store: out[out_off + (R / Rs) S1 + (R % Rs) + n S2], R = tile row
   float2 alpha;
@@ -210,8 +216,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (m_valid <= 0) return;  // uniform over the CTA, before any shared state is touched
   const int a_y = job.a_y + mt * 128;
   const int nk = job.nslab * job.nchunk;
-  const int a_boxes = (m_valid + 31) >> 5, b_boxes = (job.n_valid + 31) >> 5;
-  const uint32_t tx_bytes = (uint32_t)(a_boxes + b_boxes * (CONJ ? 1 : 4)) * 2048u;
+  const int abox = args.a_box;
+  const int gcount = job.g_count, grows = gcount > 1 ? job.g_rows : m_valid;
+  const int a_boxes_g = (grows + abox - 1) / abox;         // A boxes per row group
+  const int a_rows = gcount > 1 ? gcount * grows : a_boxes_g * abox;  // tile rows that are loaded
+  const int b_boxes = (job.n_valid + 31) >> 5;
+  const uint32_t tx_bytes =
+      (uint32_t)(gcount * a_boxes_g * abox * 64) + (uint32_t)(b_boxes * (CONJ ? 1 : 4)) * 2048u;
   const int n_int = DRAIN ? (nk + kDrain - 1) / kDrain : 1;  // accumulation intervals
   constexpr uint32_t kImOff = DRAIN ? 64u : 128u;            // Im accumulator column offset
 
@@ -254,7 +265,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t full = su32(&bar_full[s]);
         const uint32_t st = su32(sm + s * kStageBytes);
         mbar_expect_tx(full, tx_bytes);
-        for (int i = 0; i < a_boxes; ++i) tma_load3(st + i * 2048, &amap, ax, a_y + 32 * i, az, full);
+        for (int g = 0; g < gcount; ++g)
+          for (int i = 0; i < a_boxes_g; ++i)
+            tma_load3(st + (g * grows + i * abox) * 64, &amap, ax, a_y + abox * i, az + g * job.g_dz, full);
         if (CONJ) {
           for (int i = 0; i < b_boxes; ++i)
             tma_load3(st + 2 * kTileBytes + i * 2048, &bmap, bx, job.b_y + 32 * i, bz, full);
@@ -355,8 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       unsigned char* st = sm + s * kStageBytes;
       float4* ah = reinterpret_cast<float4*>(st);
       float4* al = reinterpret_cast<float4*>(st + kTileBytes);
-#pragma unroll
-      for (int i = t; i < kTileBytes / 16; i += 128) {
+      for (int i = t; i < a_rows * 4; i += 128) {
         const float4 x = ah[i], h = head4(x);
         ah[i] = h;
         al[i] = tail4(x, h);
@@ -366,8 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float4* b1l = reinterpret_cast<float4*>(st + 3 * kTileBytes);
         float4* b2h = reinterpret_cast<float4*>(st + 4 * kTileBytes);
         float4* b2l = reinterpret_cast<float4*>(st + 5 * kTileBytes);
-#pragma unroll
-        for (int i = t; i < kTileBytes / 16; i += 128) {
+        for (int i = t; i < b_boxes * 128; i += 128) {
           const float4 x = b1h[i], h = head4(x), l = tail4(x, h);
           b1h[i] = h;
           b1l[i] = l;
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       obase = job.out_off + (R / args.Rs) * args.S1 + (R % args.Rs);
       ostride = args.S2;
     }
-    const bool store = ok && row < m_valid;
+    const bool store = ok && (gcount > 1 ? (row < gcount * grows && row % grows < job.g_valid) : row < m_valid);
     auto put = [&](int n, float xr, float xi) {
       if (store && n < job.n_valid)
         args.out[obase + (long long)n * ostride] =
@@ -436,7 +447,7 @@ __global__ void k_tc_reduce(const TcTile* __restrict__ tiles, const float2* __re
   const TcTile T = tiles[blockIdx.x];
   const int n = T.m_valid * T.n_valid;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int m = e / T.n_valid, j = e - m * T.n_valid;
+    const int j = e / T.m_valid, m = e - j * T.m_valid;  // consecutive threads read consecutive rows
     const float2* p = partial + (long long)T.unit_begin * slot + (long long)(T.pn0 + j) * 128 + T.pm0 + m;
     double sx = 0.0, sy = 0.0;
     for (int u = 0; u < T.unit_count; ++u) {
@@ -558,16 +569,16 @@ sgw_status get_encode(sgw_ctx* c) {
   return SGW_OK;
 }
 
-// 3-D map of FP32 data: dims (kreals, rows, slabs), boxes of 16 reals x 32 rows, 64-byte swizzle,
+// 3-D map of FP32 data: dims (kreals, rows, slabs), boxes of 16 reals x box_rows rows, 64-byte swizzle,
 // zero fill outside the tensor.
 sgw_status make_map(sgw_ctx* c, CUtensorMap* m, const void* base, long long kreals, long long rows, long long slabs,
-                    long long row_bytes, long long slab_bytes) {
+                    long long row_bytes, long long slab_bytes, int box_rows = 32) {
   CKS(get_encode(c));
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || (slab_bytes & 15) || (kreals & 3))
     return c->fail(SGW_ERR_ARG, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[3] = {(cuuint64_t)kreals, (cuuint64_t)rows, (cuuint64_t)slabs};
   cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)slab_bytes};
-  cuuint32_t box[3] = {16, 32, 1};
+  cuuint32_t box[3] = {16, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -688,6 +699,51 @@ void gram_block(std::vector<TcJob>& jobs, std::vector<TcTile>& tiles, long long 
     }
 }
 
+// Units of one small Gram block for several tau values at once: group g of the 128-row tile holds
+// the block's rows at tau tg + g (groups R = nb rounded to 8 rows apart, slabs a_zg apart), all
+// against the same B rows.  Appends the jobs and one reduction tile per tau value.
+// Returns (first unit, unit count) so that callers can add further reduction tiles.
+std::pair<long long, int> gram_stacked(std::vector<TcJob>& jobs, std::vector<TcTile>& tiles, long long slot0,
+                                       long long slot, const TcJob& proto, int nb, int G, int a_zg, int nslab,
+                                       int nchunk, const long long* out_base, int ld, int pm0, int pn0, int m_out,
+                                       int n_out) {
+  const int R = (nb + 7) & ~7;
+  const std::vector<KRange> kr = split_k(nslab, nchunk, kchunk_target(true));
+  const long long first = (long long)jobs.size() - slot0;
+  for (const KRange& r : kr) {
+    TcJob j = proto;
+    j.a_z += r.slab0 * proto.a_dz;
+    j.b_z += r.slab0 * proto.b_dz;
+    j.a_x += 16 * r.c0;
+    j.b_x += 16 * r.c0;
+    j.nslab = r.nslab;
+    j.nchunk = r.nch;
+    j.g_count = G;
+    j.g_rows = R;
+    j.g_valid = nb;
+    j.g_dz = a_zg;
+    j.m_rows = G * R;
+    j.n_valid = nb;
+    j.n_mma = round16(nb);
+    j.out_off = ((long long)jobs.size() - slot0) * slot;
+    jobs.push_back(j);
+  }
+  for (int g = 0; out_base && g < G; ++g) {
+    TcTile t{};
+    t.out_off = out_base[g];
+    t.ld = ld;
+    t.m_valid = m_out;
+    t.n_valid = n_out;
+    t.pm0 = g * R + pm0;
+    t.pn0 = pn0;
+    t.unit_begin = (int)first;
+    t.unit_count = (int)kr.size();
+    t.unit_stride = 1;
+    tiles.push_back(t);
+  }
+  return {first, (int)kr.size()};
+}
+
 int qindex(const sgw_ctx* c, int k1, int k2) {
   const int n1 = c->p.nk[0], n2 = c->p.nk[1], n3 = c->p.nk[2];
   auto iv = [&](int k, int d) { return d == 0 ? k / (n2 * n3) : d == 1 ? (k / n3) % n2 : k % n3; };
@@ -772,11 +828,9 @@ static sgw_status build_p0(sgw_ctx* c) {
   T.vg_start.assign(nt + 1, 0); T.gvg_start.assign(nt + 1, 0); T.pg_start.assign(nt + 1, 0); T.pr_start.assign(nt + 1, 0);
   const int kq = 2 * nao * nao;
   const int nch_g = (kq + 15) / 16, nch_o = (2 * nao + 15) / 16;
-  long long slot0 = 0;
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
-    if (tl == 0) slot0 = (long long)pg.size();
-    T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size(); T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size();
+    T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size();
     for (long long p = 0; p < np; ++p) {
       const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
       TcJob j{};
@@ -791,13 +845,33 @@ static sgw_status build_p0(sgw_ctx* c) {
       g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
       gvg.push_back(g);
     }
+  }
+  // Gram units per tau chunk: blocks up to 64 stack several tau values in one tile
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long slot0 = (long long)pg.size();
+    for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); }
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
       const int w = c->auxb_w[b], nb = c->auxb_n[b], s = c->auxb_start[b];
       TcJob j{};
-      j.a_y = s; j.a_z = (int)((long long)tl * np + (long long)w * Nk); j.a_dz = 1;
+      j.a_y = s; j.a_dz = 1;
       j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      gram_block(pg, pr, slot0, kSlotD, j, nb, nb, 64, Nk, nch_g, true,
-                 (long long)t * c->p_elems + c->auxb_off[b], nb);
+      if (nb <= 64) {
+        const int G = 128 / ((nb + 7) & ~7);
+        for (int tg = t0; tg < t1; tg += G) {
+          const int Gp = std::min(G, t1 - tg);
+          j.a_z = (int)((long long)(tg - t0) * np + (long long)w * Nk);
+          std::vector<long long> ob(Gp);
+          for (int g = 0; g < Gp; ++g) ob[g] = (long long)(tg + g) * c->p_elems + c->auxb_off[b];
+          gram_stacked(pg, pr, slot0, kSlotD, j, nb, Gp, (int)np, Nk, nch_g, ob.data(), nb, 0, 0, nb, nb);
+        }
+      } else {
+        for (int t = t0; t < t1; ++t) {
+          j.a_z = (int)((long long)(t - t0) * np + (long long)w * Nk);
+          gram_block(pg, pr, slot0, kSlotD, j, nb, nb, 64, Nk, nch_g, true,
+                     (long long)t * c->p_elems + c->auxb_off[b], nb);
+        }
+      }
     }
   }
   T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size(); T.pg_start[nt] = pg.size(); T.pr_start[nt] = pr.size();
@@ -857,11 +931,9 @@ static sgw_status build_sigma(sgw_ctx* c) {
   std::vector<TcTile> sr;
   T.svg_start.assign(nt + 1, 0); T.pvg_start.assign(nt + 1, 0); T.sg_start.assign(nt + 1, 0); T.sr_start.assign(nt + 1, 0);
   const int nch_o = (2 * nao + 15) / 16, kg = 2 * naux * nao, nch_g = (kg + 15) / 16;
-  long long slot0 = 0;
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
-    if (tl == 0) slot0 = (long long)sg.size();
-    T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size(); T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size();
+    T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size();
     for (long long p = 0; p < np; ++p) {
       const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
       TcJob j{};
@@ -887,23 +959,42 @@ static sgw_status build_sigma(sgw_ctx* c) {
         }
       }
     }
+  }
+  // Gram units per tau chunk: the whole nao x nao matrix per wedge point (the reduction picks the
+  // diagonal blocks); up to 64 orbitals, several tau values share one tile
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long slot0 = (long long)sg.size();
+    for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); }
     for (int w = 0; w < nw; ++w) {
       TcJob j{};
-      j.a_y = 0; j.a_z = (int)((long long)tl * np + (long long)w * Nk); j.a_dz = 1;
+      j.a_y = 0; j.a_dz = 1;
       j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const long long u0 = (long long)sg.size() - slot0;
-      // one tile of the whole nao x nao matrix (nao <= 64 drained, else <= 128); the reduction
-      // picks the diagonal blocks out of its partials
-      gram_block(sg, sr, slot0, T.slot_s, j, nao, nao, T.drain_s ? 64 : 128, Nk, nch_g, T.drain_s, 0, 0);
-      const int nunits = (int)((long long)sg.size() - slot0 - u0);
-      for (size_t b = 0; b < c->aob_off.size(); ++b) {
-        if (c->aob_w[b] != w) continue;
-        TcTile tile{};
-        const int nb = c->aob_n[b], s = c->aob_start[b];
-        tile.out_off = (long long)t * c->g_elems + c->aob_off[b];
-        tile.ld = nb; tile.m_valid = nb; tile.n_valid = nb; tile.pm0 = s; tile.pn0 = s;
-        tile.unit_begin = (int)u0; tile.unit_count = nunits; tile.unit_stride = 1;
-        sr.push_back(tile);
+      const int R = (nao + 7) & ~7;
+      const int G = T.drain_s ? 128 / R : 1;
+      for (int tg = t0; tg < t1; tg += G) {
+        const int Gp = std::min(G, t1 - tg);
+        j.a_z = (int)((long long)(tg - t0) * np + (long long)w * Nk);
+        long long u0;
+        int nunits;
+        if (T.drain_s) {
+          std::tie(u0, nunits) = gram_stacked(sg, sr, slot0, T.slot_s, j, nao, Gp, (int)np, Nk, nch_g, nullptr, 0, 0,
+                                              0, 0, 0);
+        } else {
+          u0 = (long long)sg.size() - slot0;
+          gram_block(sg, sr, slot0, T.slot_s, j, nao, nao, 128, Nk, nch_g, false, 0, 0);
+          nunits = (int)((long long)sg.size() - slot0 - u0);
+        }
+        for (int g = 0; g < Gp; ++g)
+          for (size_t b = 0; b < c->aob_off.size(); ++b) {
+            if (c->aob_w[b] != w) continue;
+            TcTile tile{};
+            const int nb = c->aob_n[b], s = c->aob_start[b];
+            tile.out_off = (long long)(tg + g) * c->g_elems + c->aob_off[b];
+            tile.ld = nb; tile.m_valid = nb; tile.n_valid = nb; tile.pm0 = g * R + s; tile.pn0 = s;
+            tile.unit_begin = (int)u0; tile.unit_count = nunits; tile.unit_stride = 1;
+            sr.push_back(tile);
+          }
       }
     }
   }
@@ -960,12 +1051,13 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   CKS(make_map(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw * 4, 8LL * nao, 8LL * nao * nao));
   // Gram operands: rows Q, contracted (i, j) re/im
   CUtensorMap mXg, mVg;
-  CKS(make_map(c, &mXg, X, 2LL * nao * nao, naux, (long long)nc * np, 8LL * nao * nao, vs * 8));
+  CKS(make_map(c, &mXg, X, 2LL * nao * nao, naux, (long long)nc * np, 8LL * nao * nao, vs * 8, 8));
   CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, np, 8LL * nao * nao, vs * 8));
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     TcArgs a{};
+    a.a_box = 32;
     a.mtiles = T.mt_vg; a.mode = 1; a.Rs = nao; a.S1 = (long long)nao * nao; a.S2 = nao;
     a.alpha = make_float2(1.f, 0.f); a.out = Zp;
     // Z'[A][j][c] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
@@ -982,6 +1074,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
     CKS(s2);
     // P0 block tiles: sum over k and (i, j) of X[Q][(i,j)] conj(V[Q'][(i,j)])
     TcArgs g{};
+    g.a_box = 8;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
     run(c, "p0_gram_tc", T.fl_pg * ntc, 1, st, [&] {
       s3 = launch_gemm<true, 4, true>(c, mXg, mVg, T.d_pg + T.pg_start[t0], T.pg_start[t1] - T.pg_start[t0], g, st);
@@ -1023,7 +1116,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   CKS(make_map(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw * 4, 8LL * nao, 8LL * nao * nao));
   CKS(make_map(c, &mX1, X1, 2LL * naux, (long long)nao * nao, (long long)nc * np, 8LL * naux, vs * 8));
   CKS(make_map(c, &mP, Pop, T.pt_k, T.pt_rows, (long long)nc * T.ninst * 4, 4LL * T.pt_k, 4LL * T.pt_k * T.pt_rows));
-  CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, nao, (long long)nc * np, 8LL * naux * nao, vs * 8));
+  CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, nao, (long long)nc * np, 8LL * naux * nao, vs * 8, 8));
   CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, np, 8LL * naux * nao, vs * 8));
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
@@ -1034,6 +1127,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     sgw_status s1 = SGW_OK, s2 = SGW_OK, s3 = SGW_OK;
     // X1T[i][b][A] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
     TcArgs a{};
+    a.a_box = 32;
     a.mtiles = T.mt_svg; a.mode = 1; a.Rs = naux; a.S1 = (long long)nao * naux; a.S2 = naux;
     a.alpha = make_float2(1.f, 0.f); a.out = X1;
     run(c, "sigma_vg_tc", T.fl_svg * ntc, 1, st, [&] {
@@ -1042,6 +1136,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     CKS(s1);
     // X2[i][A'][b] = sum_A P^q(tau)[A][A'] X1T[i][b][A]
     TcArgs b{};
+    b.a_box = 32;
     b.mtiles = T.mt_pvg; b.mode = 1; b.Rs = nao; b.S1 = (long long)naux * nao; b.S2 = nao;
     b.alpha = make_float2(1.f, 0.f); b.out = X2;
     run(c, "sigma_pvg_tc", T.fl_pvg * ntc, 1, st, [&] {
@@ -1050,6 +1145,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     CKS(s2);
     // Sigma tiles: sum over k2 and (A', b) of X2[i][(A',b)] conj(Vt[i'][(A',b)])
     TcArgs g{};
+    g.a_box = 8;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
     run(c, "sigma_gram_tc", T.fl_sg * ntc, 1, st, [&] {
       const TcJob* jb = T.d_sg + T.sg_start[t0];
