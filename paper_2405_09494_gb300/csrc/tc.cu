@@ -12,11 +12,10 @@
 // the product to about FP32 accuracy.  Sums over long contraction ranges are split into units whose
 // FP32 partial tiles are added in FP64 in a fixed order.
 //
-// One CTA = one 128-row output tile: warp 0 issues TMA loads (64-byte swizzled 32-row boxes of
-// 16 reals), warp 1 owns the tensor-memory allocation and issues the MMAs, warps 2-5 split the
-// staged operands into head and tail and, at the end, read the accumulators and store.  Every
-// wait is bounded in time; a CTA that runs out of time records SGW status "timeout", drains its
-// copies in flight, frees its tensor memory and returns.
+// The contraction kernel is persistent and warp-specialised (one CTA per SM walking its units:
+// a TMA producer warp, an MMA warp, a head/tail splitter warpgroup and two epilogue warpgroups;
+// see k_tc_persist).  Every wait is bounded in time; a CTA that runs out of time records SGW
+// status "timeout", drains its copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -44,23 +43,22 @@ struct alignas(16) TcJob {
   int a_dz = 0, b_dz = 0;  // slab increments
   int m_rows = 0;          // rows of A the job covers (tiles of 128)
   int n_valid = 0, n_mma = 16;  // stored columns; MMA width (multiple of 16, <= 128)
-  // row groups (tau stacking): g_count groups of g_rows tile rows, group g read from slab
-  // a_z + g g_dz, g_valid rows of each stored; g_count = 1: one group of m_rows rows
-  int g_count = 1, g_rows = 0, g_valid = 0, g_dz = 0;
-  int pad0 = 0, pad1 = 0, pad2 = 0;
+  int pad = 0;
   long long out_off = 0;   // partial slot (Gram) or output base (affine store)
 };
-static_assert(sizeof(TcJob) == 96, "TcJob layout");
+static_assert(sizeof(TcJob) == 64, "TcJob layout");
 
-// Output tile of a Gram reduction over the partial tiles of its units (FP64 sum in order).
+// Output tile of a Gram reduction over the partial tiles of its units (FP64 sum in order): element
+// (m, j) of the output block is row pm0 + m pm_stride, column pn0 + j of each unit's partial tile.
 struct alignas(16) TcTile {
   long long out_off;
-  int ld, m_valid, n_valid, pm0, pn0, unit_begin, unit_count, unit_stride;
+  int ld, m_valid, n_valid, pm0, pm_stride, pn0, unit_begin, unit_count, unit_stride;
 };
 
 struct TcArgs {
   int mtiles;          // 128-row tiles per job
-  int a_box;           // rows per A box of the A tensor map (8 or 32)
+  int a_box;           // rows per A box of the A tensor map (32 or 128)
+  int b_rows;          // rows per B box; the B variants sit b_rows rows apart in shared memory
   int mode;            // 0: FP32 partial tile [n][m] at out_off; 1: affine store
   long long Rs, S1, S2;  // affine store: out[out_off + (R / Rs) S1 + (R % Rs) + n S2], R = tile row
   float2 alpha;
@@ -75,8 +73,9 @@ struct TcPlan {
   std::vector<long long> svg_start, pvg_start, sg_start, sr_start;
   TcJob *d_vg = nullptr, *d_gvg = nullptr, *d_pg = nullptr, *d_svg = nullptr, *d_pvg = nullptr, *d_sg = nullptr;
   TcTile *d_pr = nullptr, *d_sr = nullptr;
+  std::vector<long long> prp_start, srp_start;  // per tau: first reduction piece
+  int2 *d_prp = nullptr, *d_srp = nullptr;
   long long max_units_p0 = 0, max_units_s = 0;
-  bool drain_s = true;   // Sigma Gram with drained accumulators (nao <= 64)
   long long slot_s = 0;  // partial slot (complex elements) of the Sigma Gram
   int mt_vg = 0, mt_svg = 0, mt_pvg = 0;
   // block tables of the orbital partition (dense G builder) and of the auxiliary blocks (P^T builder)
@@ -93,13 +92,9 @@ struct TcPlan {
 
 namespace {
 
-constexpr int kThreads = 192;
 constexpr int kTileBytes = 128 * 64;         // 128 rows x 16 fp32 (one swizzle row each)
 constexpr int kStageBytes = 6 * kTileBytes;  // A head, A tail, B1 head, B1 tail, B2 head, B2 tail
-constexpr int smem_bytes(int stages) { return stages * kStageBytes + 1024; }
-constexpr uint32_t kTmemCols = 256;          // Re accumulator in columns [0,128), Im in [128,256)
 constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s
-constexpr int kSlot = 128 * 128;             // complex elements of one partial tile (N <= 128)
 constexpr int kSlotD = 128 * 64;             // same, drained kernels (N <= 64)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -145,6 +140,14 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, int x, int y, int v, int z,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(v), "r"(z), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -193,56 +196,80 @@ __device__ __forceinline__ float4 tail4(float4 x, float4 h) {
 // (re, im) -> (-im, re) for the two complex numbers of a float4: i times the value
 __device__ __forceinline__ float4 rot4(float4 a) { return make_float4(-a.y, a.x, -a.w, a.z); }
 
-// DRAIN: the accumulator is double-buffered in tensor memory (columns [0,128) and [128,256), Re
-// then Im, N <= 64) and emptied every kDrain chunks into FP32 registers of the epilogue warps
-// (round-to-nearest adds).  The tensor core's own accumulation truncates; draining keeps each
-// truncated chain to 6 kDrain MMAs, so the result keeps FP32 accuracy over long contractions.
+// Persistent, warp-specialised contraction kernel.  One CTA per SM walks the units
+// u = blockIdx.x, blockIdx.x + gridDim.x, ...; the shared-memory stage ring and the
+// tensor-memory accumulator ring run on across units, so the loads of one tile overlap the
+// MMAs and the stores of the previous ones.
+//   warp 0        TMA producer (one lane): the boxes of one chunk per stage
+//   warp 1        tensor-memory owner; one lane issues 12 MMAs per chunk
+//   warps 4-7     splitter: TF32 head and tail of the staged operands (and the B variants of
+//                 the Gram form) in shared memory
+//   warps 8-15    epilogue, two warpgroups, each one half of the accumulator columns (a warp
+//                 reads the 32 tensor-memory lanes of its rank within the warpgroup)
+// DRAIN: accumulator ring of 4 buffers of 128 columns (Re 64, Im 64); every kDrain chunks the
+// MMA warp moves to the next buffer and the epilogue adds the finished one into round-to-nearest
+// FP32 registers (the tensor core's own accumulation truncates), storing them at the end of the
+// unit.  Without DRAIN: 2 buffers of 256 columns (Re 128, Im 128), one per unit, read once.
+// All waits are bounded in time (status SGW_ERR_TIMEOUT, copies drained, tensor memory freed).
 constexpr int kDrain = 2;
+constexpr int kPThreads = 512;
+constexpr int kPStages = 4;
+constexpr int kPSmem = kPStages * kStageBytes + 1024;
 
-template <bool CONJ, int kStages, bool DRAIN>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_cgemm(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-               const TcJob* __restrict__ jobs, const TcArgs args, int* __restrict__ status) {
+struct UnitInfo {
+  TcJob job;
+  int mt, m_valid, a_y, nk;
+};
+
+// Jobs are read one unit ahead (the load of the next job is in flight while the current unit
+// runs), so that no role waits on a global load at a unit boundary.
+__device__ __forceinline__ TcJob load_job(const TcJob* __restrict__ jobs, const TcArgs& args, long long u,
+                                          long long nunits) {
+  return jobs[(u < nunits ? u : nunits - 1) / args.mtiles];
+}
+__device__ __forceinline__ bool unit_info(const TcJob& job, const TcArgs& args, long long u, UnitInfo& ui) {
+  ui.job = job;
+  ui.mt = (int)(u % args.mtiles);
+  ui.m_valid = min(128, ui.job.m_rows - ui.mt * 128);
+  ui.a_y = ui.job.a_y + ui.mt * 128;
+  ui.nk = ui.job.nslab * ui.job.nchunk;
+  return ui.m_valid > 0 && ui.nk > 0;
+}
+
+template <bool CONJ, bool DRAIN>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_tc_persist(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                 const TcJob* __restrict__ jobs, const TcArgs args, long long nunits, int* __restrict__ status) {
+  constexpr int NB = DRAIN ? 4 : 2;                 // accumulator buffers
+  constexpr uint32_t kBufCols = DRAIN ? 128u : 256u;
+  constexpr uint32_t kImOff = DRAIN ? 64u : 128u;   // Im accumulator column offset in a buffer
+  constexpr int kHalf = DRAIN ? 32 : 64;            // columns per epilogue warpgroup
   extern __shared__ unsigned char dsm_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages], bar_acc[2], bar_drained[2];
+  __shared__ __align__(8) uint64_t bar_full[kPStages], bar_ready[kPStages], bar_empty[kPStages];
+  __shared__ __align__(8) uint64_t bar_accf[NB], bar_acce[NB], bar_done;
   __shared__ uint32_t tmem_holder;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TcJob job = jobs[blockIdx.x / args.mtiles];
-  const int mt = blockIdx.x % args.mtiles;
-  const int m_valid = min(128, job.m_rows - mt * 128);
-  if (m_valid <= 0) return;  // uniform over the CTA, before any shared state is touched
-  const int a_y = job.a_y + mt * 128;
-  const int nk = job.nslab * job.nchunk;
-  const int abox = args.a_box;
-  const int gcount = job.g_count, grows = gcount > 1 ? job.g_rows : m_valid;
-  const int a_boxes_g = (grows + abox - 1) / abox;         // A boxes per row group
-  const int a_rows = gcount > 1 ? gcount * grows : a_boxes_g * abox;  // tile rows that are loaded
-  const int b_boxes = (job.n_valid + 31) >> 5;
-  const uint32_t tx_bytes =
-      (uint32_t)(gcount * a_boxes_g * abox * 64) + (uint32_t)(b_boxes * (CONJ ? 1 : 4)) * 2048u;
-  const int n_int = DRAIN ? (nk + kDrain - 1) / kDrain : 1;  // accumulation intervals
-  constexpr uint32_t kImOff = DRAIN ? 64u : 128u;            // Im accumulator column offset
-
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kPStages; ++s) {
       mbar_init(su32(&bar_full[s]), 1);
       mbar_init(su32(&bar_ready[s]), 128);
       mbar_init(su32(&bar_empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(su32(&bar_acc[b]), 1);
-      mbar_init(su32(&bar_drained[b]), 128);
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(su32(&bar_accf[b]), 1);
+      mbar_init(su32(&bar_acce[b]), 256);
     }
+    mbar_init(su32(&bar_done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_holder)),
-                 "r"(kTmemCols)
+                 "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -250,183 +277,241 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_after();
   const uint32_t tmem = tmem_holder;
+  const long long u_step = gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---- producer: TMA boxes of one chunk per stage
-      int issued_round[kStages];
-      for (int s = 0; s < kStages; ++s) issued_round[s] = -1;
-      for (int kk = 0; kk < nk; ++kk) {
-        const int s = kk % kStages, round = kk / kStages;
-        if (round > 0 && !mbar_wait(su32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
-        const int slab = kk / job.nchunk, ch = kk - slab * job.nchunk;
-        const int ax = job.a_x + 16 * ch, bx = job.b_x + 16 * ch;
-        const int az = job.a_z + slab * job.a_dz, bz = job.b_z + slab * job.b_dz;
-        const uint32_t full = su32(&bar_full[s]);
-        const uint32_t st = su32(sm + s * kStageBytes);
-        mbar_expect_tx(full, tx_bytes);
-        for (int g = 0; g < gcount; ++g)
-          for (int i = 0; i < a_boxes_g; ++i)
-            tma_load3(st + (g * grows + i * abox) * 64, &amap, ax, a_y + abox * i, az + g * job.g_dz, full);
-        if (CONJ) {
-          for (int i = 0; i < b_boxes; ++i)
-            tma_load3(st + 2 * kTileBytes + i * 2048, &bmap, bx, job.b_y + 32 * i, bz, full);
-        } else {
-          for (int v = 0; v < 4; ++v)
-            for (int i = 0; i < b_boxes; ++i)
-              tma_load3(st + (2 + v) * kTileBytes + i * 2048, &bmap, bx, job.b_y + 32 * i, 4 * bz + v, full);
+      // ---- producer
+      long long gk = 0;  // chunk counter over all units of this CTA
+      UnitInfo ui;
+      TcJob nxt = load_job(jobs, args, blockIdx.x, nunits);
+      for (long long u = blockIdx.x; u < nunits && !abort_flag; u += u_step) {
+        const TcJob cur = nxt;
+        nxt = load_job(jobs, args, u + u_step, nunits);
+        if (!unit_info(cur, args, u, ui)) continue;
+        const TcJob& job = ui.job;
+        const int abox = args.a_box;
+        const int a_boxes = (ui.m_valid + abox - 1) / abox;
+        const uint32_t tx_bytes = (uint32_t)(a_boxes * abox * 64) + (uint32_t)(args.b_rows * 64 * (CONJ ? 1 : 4));
+        bool ok = true;
+        for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
+          const int s = (int)(gk % kPStages);
+          const long long round = gk / kPStages;
+          if (round > 0 && !mbar_wait(su32(&bar_empty[s]), (uint32_t)((round - 1) & 1), &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int slab = kk / job.nchunk, ch = kk - slab * job.nchunk;
+          const int ax = job.a_x + 16 * ch, bx = job.b_x + 16 * ch;
+          const int az = job.a_z + slab * job.a_dz, bz = job.b_z + slab * job.b_dz;
+          const uint32_t full = su32(&bar_full[s]);
+          const uint32_t st = su32(sm + s * kStageBytes);
+          mbar_expect_tx(full, tx_bytes);
+          for (int i = 0; i < a_boxes; ++i) tma_load3(st + i * abox * 64, &amap, ax, ui.a_y + abox * i, az, full);
+          if (CONJ)
+            tma_load3(st + 2 * kTileBytes, &bmap, bx, job.b_y, bz, full);
+          else  // the four variants in one box: [variant][b_rows rows][16 reals]
+            tma_load4(st + 2 * kTileBytes, &bmap, bx, job.b_y, 0, bz, full);
         }
-        issued_round[s] = round;
+        if (!ok) break;
       }
-      // copies still in flight must land before the CTA exits
-      for (int s = 0; s < kStages; ++s)
-        if (issued_round[s] >= 0) mbar_wait(su32(&bar_full[s]), issued_round[s] & 1, &abort_flag, false);
+      // copies still in flight must land before the CTA exits: the last chunk issued on stage s
+      // is the largest g < gk with g = s (mod stages)
+      for (int s = 0; s < kPStages; ++s)
+        if (gk > s) mbar_wait(su32(&bar_full[s]), (uint32_t)(((gk - 1 - s) / kPStages) & 1), &abort_flag, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer: 2 K-steps of 8 per chunk, three TF32 products per real contraction
-      const uint32_t idesc = tf32_idesc(job.n_mma);
-      uint32_t t_re = tmem, t_im = tmem + kImOff;
-      bool fresh = true;  // next MMA into each accumulator overwrites it
-      int committed = -1;  // last interval whose completion was committed
-      for (int kk = 0; kk < nk; ++kk) {
-        if (DRAIN && kk % kDrain == 0) {
-          const int i = kk / kDrain, b = i & 1;
-          if (i >= 2 && !mbar_wait(su32(&bar_drained[b]), ((i - 2) >> 1) & 1, &abort_flag)) break;
-          t_re = tmem + 128u * b;
-          t_im = t_re + kImOff;
-          fresh = true;
-        }
-        const int s = kk % kStages, round = kk / kStages;
-        if (!mbar_wait(su32(&bar_ready[s]), round & 1, &abort_flag)) break;
-        tc_after();
-        const uint32_t base = su32(sm + s * kStageBytes);
+      // ---- MMA issuer
+      long long gk = 0, gi = 0;  // chunk and accumulator-interval counters over all units
+      UnitInfo ui;
+      bool ok = true;
+      TcJob nxt = load_job(jobs, args, blockIdx.x, nunits);
+      for (long long u = blockIdx.x; u < nunits && ok; u += u_step) {
+        const TcJob cur = nxt;
+        nxt = load_job(jobs, args, u + u_step, nunits);
+        if (!unit_info(cur, args, u, ui)) continue;
+        const uint32_t idesc = tf32_idesc(ui.job.n_mma);
+        const int per = DRAIN ? kDrain : ui.nk;  // chunks per accumulator interval
+        uint32_t t_re = 0, t_im = 0;
+        bool fresh = true;
+        for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
+          if (kk % per == 0) {
+            const int b = (int)(gi % NB);
+            if (gi >= NB && !mbar_wait(su32(&bar_acce[b]), (uint32_t)(((gi / NB) - 1) & 1), &abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_after();
+            t_re = tmem + kBufCols * b;
+            t_im = t_re + kImOff;
+            fresh = true;
+          }
+          const int s = (int)(gk % kPStages);
+          const long long round = gk / kPStages;
+          if (!mbar_wait(su32(&bar_ready[s]), (uint32_t)(round & 1), &abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_after();
+          const uint32_t base = su32(sm + s * kStageBytes);
 #pragma unroll
-        for (int sub = 0; sub < 2; ++sub) {
-          const uint32_t o = 32u * sub;
-          const uint64_t ah = sw64_desc(base + o), al = sw64_desc(base + kTileBytes + o);
-          const uint64_t b1h = sw64_desc(base + 2 * kTileBytes + o), b1l = sw64_desc(base + 3 * kTileBytes + o);
-          const uint64_t b2h = sw64_desc(base + 4 * kTileBytes + o), b2l = sw64_desc(base + 5 * kTileBytes + o);
-          const uint32_t acc = (fresh && sub == 0) ? 0u : 1u;
-          umma_tf32(t_re, al, b1h, idesc, acc);
-          umma_tf32(t_re, ah, b1l, idesc, 1u);
-          umma_tf32(t_re, ah, b1h, idesc, 1u);
-          umma_tf32(t_im, al, b2h, idesc, acc);
-          umma_tf32(t_im, ah, b2l, idesc, 1u);
-          umma_tf32(t_im, ah, b2h, idesc, 1u);
-        }
-        fresh = false;
-        umma_commit(su32(&bar_empty[s]));
-        if (DRAIN && (kk % kDrain == kDrain - 1 || kk == nk - 1)) {
-          umma_commit(su32(&bar_acc[(kk / kDrain) & 1]));
-          committed = kk / kDrain;
-        }
-      }
-      // also after an abort: the remaining completion barriers track the MMAs in flight
-      if (DRAIN) {
-        for (int i = committed + 1; i < n_int; ++i) umma_commit(su32(&bar_acc[i & 1]));
-      } else {
-        umma_commit(su32(&bar_acc[0]));
-      }
-    }
-  } else {
-    // ---- splitter (head and tail of the staged operands), drains, epilogue
-    const int t = threadIdx.x - 64;
-    const int q = warp & 3;
-    const int row = 32 * q + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
-    float acc_re[DRAIN ? 64 : 1], acc_im[DRAIN ? 64 : 1];
-#pragma unroll
-    for (int j = 0; j < (DRAIN ? 64 : 1); ++j) acc_re[j] = acc_im[j] = 0.f;
-    int next_drain = 0;
-    bool drain_ok = true;
-    auto drain = [&](int i) {
-      const int b = i & 1;
-      if (!mbar_wait(su32(&bar_acc[b]), (i >> 1) & 1, &abort_flag, false)) drain_ok = false;
-      tc_after();
-      const uint32_t base = lane_addr + 128u * b;
-#pragma unroll
-      for (int n0 = 0; n0 < 64; n0 += 16) {
-        if (n0 < job.n_mma) {
-          uint32_t re[16], im[16];
-          tmem_ld16(base + n0, re);
-          tmem_ld16(base + kImOff + n0, im);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            acc_re[(n0 + j) & (DRAIN ? 63 : 0)] += __uint_as_float(re[j]);
-            acc_im[(n0 + j) & (DRAIN ? 63 : 0)] += __uint_as_float(im[j]);
+          for (int sub = 0; sub < 2; ++sub) {
+            const uint32_t o = 32u * sub;
+            const uint64_t ah = sw64_desc(base + o), al = sw64_desc(base + kTileBytes + o);
+            const uint32_t bb = base + 2 * kTileBytes + o, vs = (uint32_t)args.b_rows * 64u;
+            const uint64_t b1h = sw64_desc(bb), b1l = sw64_desc(bb + vs);
+            const uint64_t b2h = sw64_desc(bb + 2 * vs), b2l = sw64_desc(bb + 3 * vs);
+            const uint32_t acc = (fresh && sub == 0) ? 0u : 1u;
+            umma_tf32(t_re, al, b1h, idesc, acc);
+            umma_tf32(t_re, ah, b1l, idesc, 1u);
+            umma_tf32(t_re, ah, b1h, idesc, 1u);
+            umma_tf32(t_im, al, b2h, idesc, acc);
+            umma_tf32(t_im, ah, b2l, idesc, 1u);
+            umma_tf32(t_im, ah, b2h, idesc, 1u);
+          }
+          fresh = false;
+          umma_commit(su32(&bar_empty[s]));
+          if (kk % per == per - 1 || kk == ui.nk - 1) {
+            umma_commit(su32(&bar_accf[gi % NB]));
+            ++gi;
           }
         }
       }
-      tc_before();
-      mbar_arrive(su32(&bar_drained[b]));
-    };
-    for (int kk = 0; kk < nk; ++kk) {
-      const int s = kk % kStages, round = kk / kStages;
-      if (!mbar_wait(su32(&bar_full[s]), round & 1, &abort_flag)) break;
-      unsigned char* st = sm + s * kStageBytes;
-      float4* ah = reinterpret_cast<float4*>(st);
-      float4* al = reinterpret_cast<float4*>(st + kTileBytes);
-      for (int i = t; i < a_rows * 4; i += 128) {
-        const float4 x = ah[i], h = head4(x);
-        ah[i] = h;
-        al[i] = tail4(x, h);
-      }
-      if (CONJ) {
-        float4* b1h = reinterpret_cast<float4*>(st + 2 * kTileBytes);
-        float4* b1l = reinterpret_cast<float4*>(st + 3 * kTileBytes);
-        float4* b2h = reinterpret_cast<float4*>(st + 4 * kTileBytes);
-        float4* b2l = reinterpret_cast<float4*>(st + 5 * kTileBytes);
-        for (int i = t; i < b_boxes * 128; i += 128) {
-          const float4 x = b1h[i], h = head4(x), l = tail4(x, h);
-          b1h[i] = h;
-          b1l[i] = l;
-          b2h[i] = rot4(h);
-          b2l[i] = rot4(l);
+      // every MMA issued so far has completed once bar_done fires
+      umma_commit(su32(&bar_done));
+      mbar_wait(su32(&bar_done), 0, &abort_flag, false);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---- splitter
+    const int t = threadIdx.x - 128;
+    long long gk = 0;
+    UnitInfo ui;
+    bool ok = true;
+    TcJob nxt = load_job(jobs, args, blockIdx.x, nunits);
+    for (long long u = blockIdx.x; u < nunits && ok; u += u_step) {
+      const TcJob cur = nxt;
+      nxt = load_job(jobs, args, u + u_step, nunits);
+      if (!unit_info(cur, args, u, ui)) continue;
+      const int a_rows = (ui.m_valid + args.a_box - 1) / args.a_box * args.a_box;  // rows the TMA loaded
+      for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
+        const int s = (int)(gk % kPStages);
+        const long long round = gk / kPStages;
+        if (!mbar_wait(su32(&bar_full[s]), (uint32_t)(round & 1), &abort_flag)) {
+          ok = false;
+          break;
         }
+        unsigned char* st = sm + s * kStageBytes;
+        float4* ah = reinterpret_cast<float4*>(st);
+        float4* al = reinterpret_cast<float4*>(st + kTileBytes);
+        float4 xa[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (t + 128 * r < a_rows * 4) xa[r] = ah[t + 128 * r];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (t + 128 * r < a_rows * 4) {
+            const float4 h = head4(xa[r]);
+            ah[t + 128 * r] = h;
+            al[t + 128 * r] = tail4(xa[r], h);
+          }
+        if (CONJ) {
+          const int vstride = args.b_rows * 4;  // float4s between variants
+          float4* b1h = reinterpret_cast<float4*>(st + 2 * kTileBytes);
+          float4* b1l = b1h + vstride;
+          float4* b2h = b1h + 2 * vstride;
+          float4* b2l = b1h + 3 * vstride;
+          float4 xb[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (t + 128 * r < vstride) xb[r] = b1h[t + 128 * r];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (t + 128 * r < vstride) {
+              const int i = t + 128 * r;
+              const float4 h = head4(xb[r]), l = tail4(xb[r], h);
+              b1h[i] = h;
+              b1l[i] = l;
+              b2h[i] = rot4(h);
+              b2l[i] = rot4(l);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(su32(&bar_ready[s]));
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(su32(&bar_ready[s]));
-      // after the last chunk of interval i, empty the other buffer (interval i - 1)
-      if (DRAIN && (kk % kDrain == kDrain - 1) && kk / kDrain >= 1) drain(next_drain++);
     }
-    bool ok;
-    if (DRAIN) {
-      while (next_drain < n_int) drain(next_drain++);  // bounded waits; MMAs in flight finish first
-      ok = drain_ok && !abort_flag;
-    } else {
-      // accumulators complete (bounded wait, regardless of an abort: MMAs in flight must finish)
-      ok = mbar_wait(su32(&bar_acc[0]), 0, &abort_flag, false) && !abort_flag;
-      tc_after();
-    }
-    const long long R = (long long)a_y + row;
-    long long obase;
-    long long ostride;
-    if (args.mode == 0) {
-      obase = job.out_off + row;
-      ostride = 128;
-    } else {
-      obase = job.out_off + (R / args.Rs) * args.S1 + (R % args.Rs);
-      ostride = args.S2;
-    }
-    const bool store = ok && (gcount > 1 ? (row < gcount * grows && row % grows < job.g_valid) : row < m_valid);
-    auto put = [&](int n, float xr, float xi) {
-      if (store && n < job.n_valid)
-        args.out[obase + (long long)n * ostride] =
-            make_float2(args.alpha.x * xr - args.alpha.y * xi, args.alpha.x * xi + args.alpha.y * xr);
-    };
-    if (DRAIN) {
+  } else if (warp >= 8) {
+    // ---- epilogue: warpgroup (warp - 8) / 4 owns columns [half * kHalf, half * kHalf + kHalf)
+    const int half = (warp - 8) >> 2;
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    const int c0 = half * kHalf;
+    long long gi = 0;
+    UnitInfo ui;
+    bool ok = true;
+    float acc_re[DRAIN ? kHalf : 1], acc_im[DRAIN ? kHalf : 1];
+    TcJob nxt = load_job(jobs, args, blockIdx.x, nunits);
+    for (long long u = blockIdx.x; u < nunits && ok; u += u_step) {
+      const TcJob cur = nxt;
+      nxt = load_job(jobs, args, u + u_step, nunits);
+      if (!unit_info(cur, args, u, ui)) continue;
+      const TcJob& job = ui.job;
+      const int n_int = DRAIN ? (ui.nk + kDrain - 1) / kDrain : 1;
+      const bool mine = c0 < job.n_mma;  // uniform over the warpgroup
 #pragma unroll
-      for (int j = 0; j < 64; ++j) put(j, acc_re[j & (DRAIN ? 63 : 0)], acc_im[j & (DRAIN ? 63 : 0)]);
-    } else {
-      for (int n0 = 0; n0 < job.n_mma; n0 += 16) {
-        uint32_t re[16], im[16];
-        tmem_ld16(lane_addr + n0, re);
-        tmem_ld16(lane_addr + kImOff + n0, im);
-        tmem_wait_ld();
+      for (int j = 0; j < (DRAIN ? kHalf : 1); ++j) acc_re[j] = acc_im[j] = 0.f;
+      const long long R = (long long)ui.a_y + row;
+      long long obase, ostride;
+      if (args.mode == 0) {
+        obase = job.out_off + row;
+        ostride = 128;
+      } else {
+        obase = job.out_off + (R / args.Rs) * args.S1 + (R % args.Rs);
+        ostride = args.S2;
+      }
+      const bool store_row = row < ui.m_valid;
+      auto put = [&](int n, float xr, float xi) {
+        if (store_row && n < job.n_valid)
+          args.out[obase + (long long)n * ostride] =
+              make_float2(args.alpha.x * xr - args.alpha.y * xi, args.alpha.x * xi + args.alpha.y * xr);
+      };
+      for (int it = 0; it < n_int; ++it, ++gi) {
+        const int b = (int)(gi % NB);
+        if (!mbar_wait(su32(&bar_accf[b]), (uint32_t)((gi / NB) & 1), &abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_after();
+        const uint32_t base = lane_addr + kBufCols * b + c0;
+        if (mine) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) put(n0 + j, __uint_as_float(re[j]), __uint_as_float(im[j]));
+          for (int n0 = 0; n0 < kHalf; n0 += 16) {
+            if (c0 + n0 < job.n_mma) {
+              uint32_t re[16], im[16];
+              tmem_ld16(base + n0, re);
+              tmem_ld16(base + kImOff + n0, im);
+              tmem_wait_ld();
+              if (DRAIN) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  acc_re[(n0 + j) & (DRAIN ? kHalf - 1 : 0)] += __uint_as_float(re[j]);
+                  acc_im[(n0 + j) & (DRAIN ? kHalf - 1 : 0)] += __uint_as_float(im[j]);
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) put(c0 + n0 + j, __uint_as_float(re[j]), __uint_as_float(im[j]));
+              }
+            }
+          }
+        }
+        tc_before();
+        mbar_arrive(su32(&bar_acce[b]));
+      }
+      if (!ok) break;
+      if (DRAIN && mine) {
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) put(c0 + j, acc_re[j & (DRAIN ? kHalf - 1 : 0)], acc_im[j & (DRAIN ? kHalf - 1 : 0)]);
       }
     }
   }
@@ -435,28 +520,40 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) {
     __syncwarp();
     tc_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
   if (threadIdx.x == 0 && abort_flag) atomicExch(status, (int)DEV_TIMEOUT);
 }
 
 // out[tile] = alpha * sum over the tile's units of their FP32 partial tiles ([n][128] slots),
-// summed in FP64 in a fixed order.
-__global__ void k_tc_reduce(const TcTile* __restrict__ tiles, const float2* __restrict__ partial,
-                            double2* __restrict__ out, double2 alpha, long long slot) {
-  const TcTile T = tiles[blockIdx.x];
-  const int n = T.m_valid * T.n_valid;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int j = e / T.m_valid, m = e - j * T.m_valid;  // consecutive threads read consecutive rows
-    const float2* p = partial + (long long)T.unit_begin * slot + (long long)(T.pn0 + j) * 128 + T.pm0 + m;
-    double sx = 0.0, sy = 0.0;
-    for (int u = 0; u < T.unit_count; ++u) {
-      const float2 v = p[(long long)u * T.unit_stride * slot];
-      sx += v.x;
-      sy += v.y;
+// summed in FP64 in a fixed order.  One CTA per piece of 256 elements of one tile.
+__global__ void k_tc_reduce(const TcTile* __restrict__ tiles, const int2* __restrict__ pieces,
+                            const float2* __restrict__ partial, double2* __restrict__ out, double2 alpha,
+                            long long slot) {
+  const int2 pc = pieces[blockIdx.x];
+  const TcTile T = tiles[pc.x];
+  const int e = pc.y + threadIdx.x;
+  if (e >= T.m_valid * T.n_valid) return;
+  const int j = e / T.m_valid, m = e - j * T.m_valid;  // consecutive threads read consecutive rows
+  const float2* p = partial + (long long)T.unit_begin * slot + (long long)(T.pn0 + j) * 128 + T.pm0 + m * T.pm_stride;
+  const long long us = (long long)T.unit_stride * slot;
+  double sx[4] = {0.0, 0.0, 0.0, 0.0}, sy[4] = {0.0, 0.0, 0.0, 0.0};
+  int u = 0;
+  for (; u + 4 <= T.unit_count; u += 4) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float2 v = p[(long long)(u + r) * us];
+      sx[r] += v.x;
+      sy[r] += v.y;
     }
-    out[T.out_off + (long long)m * T.ld + j] = make_double2(alpha.x * sx - alpha.y * sy, alpha.x * sy + alpha.y * sx);
   }
+  for (; u < T.unit_count; ++u) {
+    const float2 v = p[(long long)u * us];
+    sx[0] += v.x;
+    sy[0] += v.y;
+  }
+  const double ax = (sx[0] + sx[1]) + (sx[2] + sx[3]), ay = (sy[0] + sy[1]) + (sy[2] + sy[3]);
+  out[T.out_off + (long long)m * T.ld + j] = make_double2(alpha.x * ax - alpha.y * ay, alpha.x * ay + alpha.y * ax);
 }
 
 // TF32 head and TF32 tail of a double: head + tail = x to about 2^-22 relative.
@@ -587,27 +684,48 @@ sgw_status make_map(sgw_ctx* c, CUtensorMap* m, const void* base, long long krea
   return SGW_OK;
 }
 
-constexpr int kMaxDev = 64;
-bool g_attr_done[2][2][2][kMaxDev] = {};
+// 4-D map of the B operands that carry four variants: dims (kreals, rows, 4, slabs), one box of
+// 16 reals x box_rows rows x 4 variants per chunk.
+sgw_status make_map4(sgw_ctx* c, CUtensorMap* m, const void* base, long long kreals, long long rows, long long slabs,
+                     long long row_bytes, long long var_bytes, long long slab_bytes, int box_rows) {
+  CKS(get_encode(c));
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || (var_bytes & 15) || (slab_bytes & 15) ||
+      (kreals & 3))
+    return c->fail(SGW_ERR_ARG, "tensor-core operand not 16-byte aligned");
+  cuuint64_t dims[4] = {(cuuint64_t)kreals, (cuuint64_t)rows, 4, (cuuint64_t)slabs};
+  cuuint64_t strides[3] = {(cuuint64_t)row_bytes, (cuuint64_t)var_bytes, (cuuint64_t)slab_bytes};
+  cuuint32_t box[4] = {16, (cuuint32_t)box_rows, 4, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return c->fail(SGW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return SGW_OK;
+}
 
-// Short contractions (the orbital right-multiplies, a few chunks each) use two stages, so that two
-// CTAs share an SM and one's epilogue overlaps the other's loads; long ones use four.
-template <bool CONJ, int STAGES, bool DRAIN>
+int round32(int n) { return (n + 31) & ~31; }
+
+constexpr int kMaxDev = 64;
+bool g_attr_done[2][2][kMaxDev] = {};
+int g_sms[kMaxDev] = {};
+
+template <bool CONJ, bool DRAIN>
 sgw_status launch_gemm(sgw_ctx* c, const CUtensorMap& am, const CUtensorMap& bm, const TcJob* jobs, long long njobs,
                        const TcArgs& a, cudaStream_t st) {
   if (njobs <= 0) return SGW_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return c->fail(SGW_ERR_CUDA, "no current device");
-  bool& done = g_attr_done[CONJ][STAGES == 4][DRAIN][dev];
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm<CONJ, STAGES, DRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes(STAGES));
+  if (!g_attr_done[CONJ][DRAIN][dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_persist<CONJ, DRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem);
     if (e != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string("tensor-core kernel attribute: ") + cudaGetErrorString(e));
-    done = true;
+    if (!g_sms[dev] && cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return c->fail(SGW_ERR_CUDA, "multiprocessor count");
+    g_attr_done[CONJ][DRAIN][dev] = true;
   }
-  const long long grid = njobs * a.mtiles;
-  if (grid > 0x7fffffffLL) return c->fail(SGW_ERR_ARG, "tensor-core launch too large");
-  k_tc_cgemm<CONJ, STAGES, DRAIN><<<(unsigned)grid, kThreads, smem_bytes(STAGES), st>>>(am, bm, jobs, a, c->d_status);
+  const long long nunits = njobs * a.mtiles;
+  const unsigned grid = (unsigned)std::min<long long>(nunits, g_sms[dev]);
+  // one CTA per SM (the stage ring fills most of shared memory; all 512 tensor-memory columns)
+  k_tc_persist<CONJ, DRAIN><<<grid, kPThreads, kPSmem, st>>>(am, bm, jobs, a, nunits, c->d_status);
   return SGW_OK;
 }
 
@@ -655,93 +773,81 @@ std::vector<KRange> split_k(int nslab, int nchunk, long long target) {
   return out;
 }
 
-// Units of one Gram output block (rows [r0, r0 + nb) of A against rows [c0, c0 + nb) of B, or the
-// given extents), tiles of 128 x ntile, ordered K range first so that the tiles of one K range run
-// side by side and share their operand loads in L2.  Appends jobs and reduction tiles.
-void gram_block(std::vector<TcJob>& jobs, std::vector<TcTile>& tiles, long long slot0, long long slot,
-                const TcJob& proto, int mrows, int ncols, int ntile, int nslab, int nchunk, bool drained,
-                long long out_base, int ld) {
-  const int mts = (mrows + 127) / 128, nts = (ncols + ntile - 1) / ntile;
-  const std::vector<KRange> kr = split_k(nslab, nchunk, kchunk_target(drained));
-  const long long first = (long long)jobs.size() - slot0;
+// Gram units over a tau-interleaved A operand: row r of the contraction for local tau tl is row
+// r nc + tl of its pair slab, so one 128-row tile holds rpt = 128 / nc values of r for all tau
+// values of a chunk against the same B rows.  Rows [r0, r0 + nr) of A against B rows
+// [b_y, b_y + ncols) in tiles of 128 x ntile, ordered K range first (the tiles of one K range run
+// side by side and share their loads in L2).  Appends the jobs.
+struct GramTiles {
+  long long first;     // first unit (relative to the chunk's first unit)
+  int count, stride;   // units per tile, unit stride between the K ranges of one tile
+  int mts, nts, rpt, ntile;
+};
+GramTiles gram_interleaved(std::vector<TcJob>& jobs, long long slot0, long long slot, const TcJob& proto, int r0,
+                           int nr, int nc, int ncols, int ntile, int nslab, int nchunk) {
+  GramTiles g;
+  g.rpt = 128 / nc;
+  g.ntile = ntile;
+  g.mts = (nr + g.rpt - 1) / g.rpt;
+  g.nts = (ncols + ntile - 1) / ntile;
+  const std::vector<KRange> kr = split_k(nslab, nchunk, kchunk_target(true));
+  g.first = (long long)jobs.size() - slot0;
+  g.count = (int)kr.size();
+  g.stride = g.mts * g.nts;
   for (const KRange& r : kr)
-    for (int mi = 0; mi < mts; ++mi)
-      for (int ni = 0; ni < nts; ++ni) {
+    for (int mi = 0; mi < g.mts; ++mi)
+      for (int ni = 0; ni < g.nts; ++ni) {
         TcJob j = proto;
-        j.a_y += 128 * mi;
-        j.b_y += ntile * ni;
+        j.a_y = (r0 + mi * g.rpt) * nc;
+        j.m_rows = std::min(g.rpt, nr - mi * g.rpt) * nc;
+        j.b_y = proto.b_y + ntile * ni;
         j.a_z += r.slab0 * proto.a_dz;
         j.b_z += r.slab0 * proto.b_dz;
         j.a_x += 16 * r.c0;
         j.b_x += 16 * r.c0;
         j.nslab = r.nslab;
         j.nchunk = r.nch;
-        j.m_rows = std::min(128, mrows - 128 * mi);
         j.n_valid = std::min(ntile, ncols - ntile * ni);
         j.n_mma = round16(j.n_valid);
         j.out_off = ((long long)jobs.size() - slot0) * slot;
         jobs.push_back(j);
       }
-  if (ld <= 0) return;  // caller adds its own reduction tiles
-  for (int mi = 0; mi < mts; ++mi)
-    for (int ni = 0; ni < nts; ++ni) {
-      TcTile t{};
-      t.out_off = out_base + (long long)(128 * mi) * ld + ntile * ni;
-      t.ld = ld;
-      t.m_valid = std::min(128, mrows - 128 * mi);
-      t.n_valid = std::min(ntile, ncols - ntile * ni);
-      t.pm0 = 0;
-      t.pn0 = 0;
-      t.unit_begin = (int)(first + mi * nts + ni);
-      t.unit_count = (int)kr.size();
-      t.unit_stride = mts * nts;
-      tiles.push_back(t);
-    }
+  return g;
 }
 
-// Units of one small Gram block for several tau values at once: group g of the 128-row tile holds
-// the block's rows at tau tg + g (groups R = nb rounded to 8 rows apart, slabs a_zg apart), all
-// against the same B rows.  Appends the jobs and one reduction tile per tau value.
-// Returns (first unit, unit count) so that callers can add further reduction tiles.
-std::pair<long long, int> gram_stacked(std::vector<TcJob>& jobs, std::vector<TcTile>& tiles, long long slot0,
-                                       long long slot, const TcJob& proto, int nb, int G, int a_zg, int nslab,
-                                       int nchunk, const long long* out_base, int ld, int pm0, int pn0, int m_out,
-                                       int n_out) {
-  const int R = (nb + 7) & ~7;
-  const std::vector<KRange> kr = split_k(nslab, nchunk, kchunk_target(true));
-  const long long first = (long long)jobs.size() - slot0;
-  for (const KRange& r : kr) {
-    TcJob j = proto;
-    j.a_z += r.slab0 * proto.a_dz;
-    j.b_z += r.slab0 * proto.b_dz;
-    j.a_x += 16 * r.c0;
-    j.b_x += 16 * r.c0;
-    j.nslab = r.nslab;
-    j.nchunk = r.nch;
-    j.g_count = G;
-    j.g_rows = R;
-    j.g_valid = nb;
-    j.g_dz = a_zg;
-    j.m_rows = G * R;
-    j.n_valid = nb;
-    j.n_mma = round16(nb);
-    j.out_off = ((long long)jobs.size() - slot0) * slot;
-    jobs.push_back(j);
+// Reduction tiles of one output block for local tau tl: A rows [ra0, ra0 + nra) (of the range that
+// starts at r0 in gram_interleaved) against B columns [ca0, ca0 + nca), written at out_base (row
+// stride ld), split along the tiles they fall in.
+void gram_out_tiles(std::vector<TcTile>& tiles, const GramTiles& g, int r0, int nc, int tl, int ra0, int nra,
+                    int cb0, int ca0, int nca, long long out_base, int ld) {
+  for (int mi = 0; mi < g.mts; ++mi) {
+    const int tr0 = r0 + mi * g.rpt, tr1 = tr0 + g.rpt;
+    const int a0 = std::max(ra0, tr0), a1 = std::min(ra0 + nra, tr1);
+    if (a0 >= a1) continue;
+    for (int ni = 0; ni < g.nts; ++ni) {
+      const int tc0 = cb0 + ni * g.ntile, tc1 = tc0 + g.ntile;
+      const int b0 = std::max(ca0, tc0), b1 = std::min(ca0 + nca, tc1);
+      if (b0 >= b1) continue;
+      TcTile t{};
+      t.out_off = out_base + (long long)(a0 - ra0) * ld + (b0 - ca0);
+      t.ld = ld;
+      t.m_valid = a1 - a0;
+      t.n_valid = b1 - b0;
+      t.pm0 = (a0 - tr0) * nc + tl;
+      t.pm_stride = nc;
+      t.pn0 = b0 - tc0;
+      t.unit_begin = (int)(g.first + mi * g.nts + ni);
+      t.unit_count = g.count;
+      t.unit_stride = g.stride;
+      tiles.push_back(t);
+    }
   }
-  for (int g = 0; out_base && g < G; ++g) {
-    TcTile t{};
-    t.out_off = out_base[g];
-    t.ld = ld;
-    t.m_valid = m_out;
-    t.n_valid = n_out;
-    t.pm0 = g * R + pm0;
-    t.pn0 = pn0;
-    t.unit_begin = (int)first;
-    t.unit_count = (int)kr.size();
-    t.unit_stride = 1;
-    tiles.push_back(t);
-  }
-  return {first, (int)kr.size()};
+}
+
+// Launch pieces (tile, first element) of the reduction tiles [t0, t1), 256 elements each.
+void reduce_pieces(const std::vector<TcTile>& tiles, long long t0, long long t1, std::vector<int2>& out) {
+  for (long long t = t0; t < t1; ++t)
+    for (int e = 0; e < tiles[t].m_valid * tiles[t].n_valid; e += 256) out.push_back(make_int2((int)(t - t0), e));
 }
 
 int qindex(const sgw_ctx* c, int k1, int k2) {
@@ -758,7 +864,9 @@ long long tc_nc(const sgw_ctx* c) {
   const double gb = s ? std::atof(s) : 24.0;
   const double budget = gb * 1e9;
   long long nc = (long long)(budget * 0.6 / (2.0 * np * vs * sizeof(float2)));
-  return std::max(1LL, std::min<long long>(nc, c->nt));
+  nc = std::max(1LL, std::min<long long>({nc, (long long)c->nt, 128LL}));
+  const long long nchunks = (c->nt + nc - 1) / nc;
+  return (c->nt + nchunks - 1) / nchunks;  // balanced chunks
 }
 
 sgw_status tables_common(sgw_ctx* c, TcPlan& T) {
@@ -796,6 +904,7 @@ void tc_free(sgw_ctx* c) {
   if (!c->tc) return;
   TcPlan& T = *c->tc;
   fr(T.d_vg); fr(T.d_gvg); fr(T.d_pg); fr(T.d_svg); fr(T.d_pvg); fr(T.d_sg); fr(T.d_pr); fr(T.d_sr);
+  fr(T.d_prp); fr(T.d_srp);
   fr(T.d_ao_start); fr(T.d_ao_size); fr(T.d_ao_doff); fr(T.d_g_off); fr(T.d_ab_info); fr(T.d_ab_off);
   delete c->tc;
   c->tc = nullptr;
@@ -843,37 +952,30 @@ static sgw_status build_p0(sgw_ctx* c) {
       TcJob g = j;
       g.a_z = (int)((long long)tl * np + p);
       g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
+      g.out_off = p * nc * (long long)rows * nao + (long long)tl * nao * nao;  // X[p][Q][tl][i][j]
       gvg.push_back(g);
     }
   }
-  // Gram units per tau chunk: blocks up to 64 stack several tau values in one tile
+  // Gram units per tau chunk over the tau-interleaved X: rows (Q, tl) of each pair slab
+  std::vector<int2> prp;
+  T.prp_start.assign(nt + 1, 0);
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc);
-    const long long slot0 = (long long)pg.size();
-    for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); }
+    const long long slot0 = (long long)pg.size(), tile0 = (long long)pr.size();
+    for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); T.prp_start[t] = prp.size(); }
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
       const int w = c->auxb_w[b], nb = c->auxb_n[b], s = c->auxb_start[b];
       TcJob j{};
-      j.a_y = s; j.a_dz = 1;
+      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
       j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      if (nb <= 64) {
-        const int G = 128 / ((nb + 7) & ~7);
-        for (int tg = t0; tg < t1; tg += G) {
-          const int Gp = std::min(G, t1 - tg);
-          j.a_z = (int)((long long)(tg - t0) * np + (long long)w * Nk);
-          std::vector<long long> ob(Gp);
-          for (int g = 0; g < Gp; ++g) ob[g] = (long long)(tg + g) * c->p_elems + c->auxb_off[b];
-          gram_stacked(pg, pr, slot0, kSlotD, j, nb, Gp, (int)np, Nk, nch_g, ob.data(), nb, 0, 0, nb, nb);
-        }
-      } else {
-        for (int t = t0; t < t1; ++t) {
-          j.a_z = (int)((long long)(t - t0) * np + (long long)w * Nk);
-          gram_block(pg, pr, slot0, kSlotD, j, nb, nb, 64, Nk, nch_g, true,
-                     (long long)t * c->p_elems + c->auxb_off[b], nb);
-        }
-      }
+      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g);
+      for (int t = t0; t < t1; ++t)
+        gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
     }
+    reduce_pieces(pr, tile0, (long long)pr.size(), prp);
   }
+  T.prp_start[nt] = prp.size();
+  CKS(up(c, T.d_prp, prp));
   T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size(); T.pg_start[nt] = pg.size(); T.pr_start[nt] = pr.size();
   T.max_units_p0 = 0;
   for (int t0 = 0; t0 < nt; t0 += nc) {
@@ -902,8 +1004,7 @@ static sgw_status build_sigma(sgw_ctx* c) {
   const long long np = (long long)nw * Nk;
   const int nc = (int)tc_nc(c);
   T.nc_s = nc;
-  T.drain_s = nao <= 64;
-  T.slot_s = T.drain_s ? kSlotD : kSlot;
+  T.slot_s = kSlotD;
   const long long vs = (long long)naux * nao * nao;
   // auxiliary block instances (all wedge q): start, size, delta; P^T operand extents
   const int ninst = (int)c->auxb_off.size();
@@ -954,50 +1055,36 @@ static sgw_status build_sigma(sgw_ctx* c) {
           v.b_x = 0;
           v.nslab = 1; v.nchunk = (d + 2 * nb + 15) / 16;
           v.m_rows = rows_x; v.n_valid = std::min(64, nb - n0); v.n_mma = round16(v.n_valid);
-          v.out_off = ((long long)tl * np + p) * vs + (long long)(s + n0) * nao;
+          v.out_off = p * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
           pvg.push_back(v);
         }
       }
     }
   }
-  // Gram units per tau chunk: the whole nao x nao matrix per wedge point (the reduction picks the
-  // diagonal blocks); up to 64 orbitals, several tau values share one tile
+  // Gram units per tau chunk: the whole nao x nao matrix per wedge point over the tau-interleaved X2
+  // (rows (i, tl)); the reduction picks the diagonal blocks out of the partial tiles
+  std::vector<int2> srp;
+  T.srp_start.assign(nt + 1, 0);
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc);
-    const long long slot0 = (long long)sg.size();
-    for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); }
+    const long long slot0 = (long long)sg.size(), tile0 = (long long)sr.size();
+    for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); T.srp_start[t] = srp.size(); }
     for (int w = 0; w < nw; ++w) {
       TcJob j{};
-      j.a_y = 0; j.a_dz = 1;
+      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
       j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const int R = (nao + 7) & ~7;
-      const int G = T.drain_s ? 128 / R : 1;
-      for (int tg = t0; tg < t1; tg += G) {
-        const int Gp = std::min(G, t1 - tg);
-        j.a_z = (int)((long long)(tg - t0) * np + (long long)w * Nk);
-        long long u0;
-        int nunits;
-        if (T.drain_s) {
-          std::tie(u0, nunits) = gram_stacked(sg, sr, slot0, T.slot_s, j, nao, Gp, (int)np, Nk, nch_g, nullptr, 0, 0,
-                                              0, 0, 0);
-        } else {
-          u0 = (long long)sg.size() - slot0;
-          gram_block(sg, sr, slot0, T.slot_s, j, nao, nao, 128, Nk, nch_g, false, 0, 0);
-          nunits = (int)((long long)sg.size() - slot0 - u0);
+      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g);
+      for (int t = t0; t < t1; ++t)
+        for (size_t b = 0; b < c->aob_off.size(); ++b) {
+          if (c->aob_w[b] != w) continue;
+          const int nb = c->aob_n[b], s = c->aob_start[b];
+          gram_out_tiles(sr, g, 0, nc, t - t0, s, nb, 0, s, nb, (long long)t * c->g_elems + c->aob_off[b], nb);
         }
-        for (int g = 0; g < Gp; ++g)
-          for (size_t b = 0; b < c->aob_off.size(); ++b) {
-            if (c->aob_w[b] != w) continue;
-            TcTile tile{};
-            const int nb = c->aob_n[b], s = c->aob_start[b];
-            tile.out_off = (long long)(tg + g) * c->g_elems + c->aob_off[b];
-            tile.ld = nb; tile.m_valid = nb; tile.n_valid = nb; tile.pm0 = g * R + s; tile.pn0 = s;
-            tile.unit_begin = (int)u0; tile.unit_count = nunits; tile.unit_stride = 1;
-            sr.push_back(tile);
-          }
-      }
     }
+    reduce_pieces(sr, tile0, (long long)sr.size(), srp);
   }
+  T.srp_start[nt] = srp.size();
+  CKS(up(c, T.d_srp, srp));
   T.svg_start[nt] = svg.size(); T.pvg_start[nt] = pvg.size(); T.sg_start[nt] = sg.size(); T.sr_start[nt] = sr.size();
   T.max_units_s = 0;
   for (int t0 = 0; t0 < nt; t0 += nc) {
@@ -1046,43 +1133,48 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   });
   CUtensorMap mV, mZ, mG;
   const long long rows = (long long)naux * nao;
-  CKS(make_map(c, &mV, c->d_V32[0], 2 * nao, rows, np, 8LL * nao, vs * 8));
-  CKS(make_map(c, &mZ, Zp, 2 * nao, rows, (long long)nc * np, 8LL * nao, vs * 8));
-  CKS(make_map(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw * 4, 8LL * nao, 8LL * nao * nao));
+  CKS(make_map(c, &mV, c->d_V32[0], 2 * nao, rows, np, 8LL * nao, vs * 8, 128));
+  CKS(make_map(c, &mZ, Zp, 2 * nao, rows, (long long)nc * np, 8LL * nao, vs * 8, 128));
+  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, round32(nao)));
   // Gram operands: rows Q, contracted (i, j) re/im
   CUtensorMap mXg, mVg;
-  CKS(make_map(c, &mXg, X, 2LL * nao * nao, naux, (long long)nc * np, 8LL * nao * nao, vs * 8, 8));
-  CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, np, 8LL * nao * nao, vs * 8));
+  CKS(make_map(c, &mXg, X, 2LL * nao * nao, (long long)naux * nc, np, 8LL * nao * nao, (long long)nc * vs * 8, 32));
+  CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, np, 8LL * nao * nao, vs * 8, 64));
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     TcArgs a{};
-    a.a_box = 32;
+    a.a_box = 128;
+    a.b_rows = round32(nao);
     a.mtiles = T.mt_vg; a.mode = 1; a.Rs = nao; a.S1 = (long long)nao * nao; a.S2 = nao;
     a.alpha = make_float2(1.f, 0.f); a.out = Zp;
     // Z'[A][j][c] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
     sgw_status s1 = SGW_OK, s2 = SGW_OK, s3 = SGW_OK;
     run(c, "p0_vg_tc", T.fl_vg * ntc, 1, st, [&] {
-      s1 = launch_gemm<false, 2, false>(c, mV, mG, T.d_vg + T.vg_start[t0], T.vg_start[t1] - T.vg_start[t0], a, st);
+      s1 = launch_gemm<false, false>(c, mV, mG, T.d_vg + T.vg_start[t0], T.vg_start[t1] - T.vg_start[t0], a, st);
     });
     CKS(s1);
-    // X[A][i][j] = sum_c G^k(-tau)[i][c] Z'[A][j][c],  G(-tau_j) = -G(tau_{n-1-j})
+    // X[A][tl][i][j] = sum_c G^k(-tau)[i][c] Z'[A][j][c],  G(-tau_j) = -G(tau_{n-1-j})
     a.alpha = make_float2(-1.f, 0.f); a.out = X;
+    a.S1 = (long long)nc * nao * nao;
     run(c, "p0_gvg_tc", T.fl_gvg * ntc, 1, st, [&] {
-      s2 = launch_gemm<false, 2, false>(c, mZ, mG, T.d_gvg + T.gvg_start[t0], T.gvg_start[t1] - T.gvg_start[t0], a, st);
+      s2 = launch_gemm<false, false>(c, mZ, mG, T.d_gvg + T.gvg_start[t0], T.gvg_start[t1] - T.gvg_start[t0], a, st);
     });
     CKS(s2);
     // P0 block tiles: sum over k and (i, j) of X[Q][(i,j)] conj(V[Q'][(i,j)])
     TcArgs g{};
-    g.a_box = 8;
+    g.a_box = 32;
+    g.b_rows = 64;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
     run(c, "p0_gram_tc", T.fl_pg * ntc, 1, st, [&] {
-      s3 = launch_gemm<true, 4, true>(c, mXg, mVg, T.d_pg + T.pg_start[t0], T.pg_start[t1] - T.pg_start[t0], g, st);
+      s3 = launch_gemm<true, true>(c, mXg, mVg, T.d_pg + T.pg_start[t0], T.pg_start[t1] - T.pg_start[t0], g, st);
     });
     CKS(s3);
-    const long long r0 = T.pr_start[t0], r1 = T.pr_start[t1];
+    const long long r0 = T.pr_start[t0], q0 = T.prp_start[t0], q1 = T.prp_start[t1];
     run(c, "gram_reduce", 0.0, 1, st, [&] {
-      if (r1 > r0) k_tc_reduce<<<(unsigned)(r1 - r0), 256, 0, st>>>(T.d_pr + r0, part, out, make_double2(alpha, 0.0), kSlotD);
+      if (q1 > q0)
+        k_tc_reduce<<<(unsigned)(q1 - q0), 256, 0, st>>>(T.d_pr + r0, T.d_prp + q0, part, out, make_double2(alpha, 0.0),
+                                                         kSlotD);
     });
   }
   return SGW_OK;
@@ -1112,12 +1204,13 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   });
   CUtensorMap mVt, mG, mX1, mP, mX2g, mVtg;
   const long long rows_v = (long long)nao * naux;
-  CKS(make_map(c, &mVt, c->d_V32[1], 2 * nao, rows_v, np, 8LL * nao, vs * 8));
-  CKS(make_map(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw * 4, 8LL * nao, 8LL * nao * nao));
-  CKS(make_map(c, &mX1, X1, 2LL * naux, (long long)nao * nao, (long long)nc * np, 8LL * naux, vs * 8));
-  CKS(make_map(c, &mP, Pop, T.pt_k, T.pt_rows, (long long)nc * T.ninst * 4, 4LL * T.pt_k, 4LL * T.pt_k * T.pt_rows));
-  CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, nao, (long long)nc * np, 8LL * naux * nao, vs * 8, 8));
-  CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, np, 8LL * naux * nao, vs * 8));
+  CKS(make_map(c, &mVt, c->d_V32[1], 2 * nao, rows_v, np, 8LL * nao, vs * 8, 128));
+  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, round32(nao)));
+  CKS(make_map(c, &mX1, X1, 2LL * naux, (long long)nao * nao, (long long)nc * np, 8LL * naux, vs * 8, 128));
+  CKS(make_map4(c, &mP, Pop, T.pt_k, T.pt_rows, (long long)nc * T.ninst, 4LL * T.pt_k, 4LL * T.pt_k * T.pt_rows,
+                16LL * T.pt_k * T.pt_rows, 64));
+  CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, (long long)nao * nc, np, 8LL * naux * nao, (long long)nc * vs * 8, 32));
+  CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, np, 8LL * naux * nao, vs * 8, 64));
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     run(c, "tc_prep", 0.0, 1, st, [&] {
@@ -1127,38 +1220,38 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     sgw_status s1 = SGW_OK, s2 = SGW_OK, s3 = SGW_OK;
     // X1T[i][b][A] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
     TcArgs a{};
-    a.a_box = 32;
+    a.a_box = 128;
+    a.b_rows = round32(nao);
     a.mtiles = T.mt_svg; a.mode = 1; a.Rs = naux; a.S1 = (long long)nao * naux; a.S2 = naux;
     a.alpha = make_float2(1.f, 0.f); a.out = X1;
     run(c, "sigma_vg_tc", T.fl_svg * ntc, 1, st, [&] {
-      s1 = launch_gemm<false, 2, false>(c, mVt, mG, T.d_svg + T.svg_start[t0], T.svg_start[t1] - T.svg_start[t0], a, st);
+      s1 = launch_gemm<false, false>(c, mVt, mG, T.d_svg + T.svg_start[t0], T.svg_start[t1] - T.svg_start[t0], a, st);
     });
     CKS(s1);
-    // X2[i][A'][b] = sum_A P^q(tau)[A][A'] X1T[i][b][A]
+    // X2[i][tl][A'][b] = sum_A P^q(tau)[A][A'] X1T[i][b][A]
     TcArgs b{};
-    b.a_box = 32;
-    b.mtiles = T.mt_pvg; b.mode = 1; b.Rs = nao; b.S1 = (long long)naux * nao; b.S2 = nao;
+    b.a_box = 128;
+    b.b_rows = 64;
+    b.mtiles = T.mt_pvg; b.mode = 1; b.Rs = nao; b.S1 = (long long)nc * naux * nao; b.S2 = nao;
     b.alpha = make_float2(1.f, 0.f); b.out = X2;
     run(c, "sigma_pvg_tc", T.fl_pvg * ntc, 1, st, [&] {
-      s2 = launch_gemm<false, 4, true>(c, mX1, mP, T.d_pvg + T.pvg_start[t0], T.pvg_start[t1] - T.pvg_start[t0], b, st);
+      s2 = launch_gemm<false, true>(c, mX1, mP, T.d_pvg + T.pvg_start[t0], T.pvg_start[t1] - T.pvg_start[t0], b, st);
     });
     CKS(s2);
-    // Sigma tiles: sum over k2 and (A', b) of X2[i][(A',b)] conj(Vt[i'][(A',b)])
+    // Sigma tiles: sum over k2 and (A', b) of X2[(i,tl)][(A',b)] conj(Vt[i'][(A',b)])
     TcArgs g{};
-    g.a_box = 8;
+    g.a_box = 32;
+    g.b_rows = 64;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
     run(c, "sigma_gram_tc", T.fl_sg * ntc, 1, st, [&] {
-      const TcJob* jb = T.d_sg + T.sg_start[t0];
-      const long long nj = T.sg_start[t1] - T.sg_start[t0];
-      s3 = T.drain_s ? launch_gemm<true, 4, true>(c, mX2g, mVtg, jb, nj, g, st)
-                     : launch_gemm<true, 4, false>(c, mX2g, mVtg, jb, nj, g, st);
+      s3 = launch_gemm<true, true>(c, mX2g, mVtg, T.d_sg + T.sg_start[t0], T.sg_start[t1] - T.sg_start[t0], g, st);
     });
     CKS(s3);
-    const long long r0 = T.sr_start[t0], r1 = T.sr_start[t1];
+    const long long r0 = T.sr_start[t0], q0 = T.srp_start[t0], q1 = T.srp_start[t1];
     run(c, "gram_reduce", 0.0, 1, st, [&] {
-      if (r1 > r0)
-        k_tc_reduce<<<(unsigned)(r1 - r0), 256, 0, st>>>(T.d_sr + r0, part, out, make_double2(-1.0 / c->Nk, 0.0),
-                                                          T.slot_s);
+      if (q1 > q0)
+        k_tc_reduce<<<(unsigned)(q1 - q0), 256, 0, st>>>(T.d_sr + r0, T.d_srp + q0, part, out,
+                                                         make_double2(-1.0 / c->Nk, 0.0), T.slot_s);
     });
   }
   return SGW_OK;
