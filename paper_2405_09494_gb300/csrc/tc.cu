@@ -161,12 +161,22 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t tf32_idesc(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
-__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// A operand in tensor memory (128 lanes = rows, 8 columns = the K step), B in shared memory
+__device__ __forceinline__ void umma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -240,10 +250,13 @@ template <bool CONJ, bool DRAIN>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_persist(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                  const TcJob* __restrict__ jobs, const TcArgs args, long long nunits, int* __restrict__ status) {
-  constexpr int NB = DRAIN ? 4 : 2;                 // accumulator buffers
-  constexpr uint32_t kBufCols = DRAIN ? 128u : 256u;
-  constexpr uint32_t kImOff = DRAIN ? 64u : 128u;   // Im accumulator column offset in a buffer
-  constexpr int kHalf = DRAIN ? 32 : 64;            // columns per epilogue warpgroup
+  // tensor memory: accumulator buffers (Re 64 + Im 64 columns each) in [0, 384), the A head and
+  // tail of the four stages (16 + 16 columns each) in [384, 512)
+  constexpr int NB = 3;                             // accumulator buffers
+  constexpr uint32_t kBufCols = 128u;
+  constexpr uint32_t kImOff = 64u;                  // Im accumulator column offset in a buffer
+  constexpr int kHalf = 32;                         // columns per epilogue warpgroup
+  constexpr uint32_t kACol = 384u;                  // A stages in tensor memory
   extern __shared__ unsigned char dsm_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_full[kPStages], bar_ready[kPStages], bar_empty[kPStages];
@@ -331,9 +344,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const TcJob cur = nxt;
         nxt = load_job(jobs, args, u + u_step, nunits);
         if (!unit_info(cur, args, u, ui)) continue;
-        const uint32_t idesc = tf32_idesc(ui.job.n_mma);
+        // one MMA per product writes Re (columns [0, b_rows)) and Im ([b_rows, 2 b_rows)) together
+        const uint32_t idesc = tf32_idesc(2 * args.b_rows);
         const int per = DRAIN ? kDrain : ui.nk;  // chunks per accumulator interval
-        uint32_t t_re = 0, t_im = 0;
+        uint32_t t_re = 0;
         bool fresh = true;
         for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
           if (kk % per == 0) {
@@ -344,7 +358,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             tc_after();
             t_re = tmem + kBufCols * b;
-            t_im = t_re + kImOff;
             fresh = true;
           }
           const int s = (int)(gk % kPStages);
@@ -358,17 +371,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
           for (int sub = 0; sub < 2; ++sub) {
             const uint32_t o = 32u * sub;
-            const uint64_t ah = sw64_desc(base + o), al = sw64_desc(base + kTileBytes + o);
+            const uint32_t ah = tmem + kACol + 32u * s + 8u * sub, al = ah + 16u;  // A head / tail in TMEM
             const uint32_t bb = base + 2 * kTileBytes + o, vs = (uint32_t)args.b_rows * 64u;
-            const uint64_t b1h = sw64_desc(bb), b1l = sw64_desc(bb + vs);
-            const uint64_t b2h = sw64_desc(bb + 2 * vs), b2l = sw64_desc(bb + 3 * vs);
+            const uint64_t bh = sw64_desc(bb), bl = sw64_desc(bb + 2 * vs);  // [head | i head], [tail | i tail]
             const uint32_t acc = (fresh && sub == 0) ? 0u : 1u;
-            umma_tf32(t_re, al, b1h, idesc, acc);
-            umma_tf32(t_re, ah, b1l, idesc, 1u);
-            umma_tf32(t_re, ah, b1h, idesc, 1u);
-            umma_tf32(t_im, al, b2h, idesc, acc);
-            umma_tf32(t_im, ah, b2l, idesc, 1u);
-            umma_tf32(t_im, ah, b2h, idesc, 1u);
+            umma_tf32_ta(t_re, al, bh, idesc, acc);
+            umma_tf32_ta(t_re, ah, bl, idesc, 1u);
+            umma_tf32_ta(t_re, ah, bh, idesc, 1u);
           }
           fresh = false;
           umma_commit(su32(&bar_empty[s]));
@@ -385,6 +394,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   } else if (warp >= 4 && warp < 8) {
     // ---- splitter
     const int t = threadIdx.x - 128;
+    const int q = warp & 3, row = 32 * q + lane;  // tensor-memory lane of this thread
     long long gk = 0;
     UnitInfo ui;
     bool ok = true;
@@ -393,7 +403,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
       const TcJob cur = nxt;
       nxt = load_job(jobs, args, u + u_step, nunits);
       if (!unit_info(cur, args, u, ui)) continue;
-      const int a_rows = (ui.m_valid + args.a_box - 1) / args.a_box * args.a_box;  // rows the TMA loaded
       for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
         const int s = (int)(gk % kPStages);
         const long long round = gk / kPStages;
@@ -402,24 +411,31 @@ __global__ void __launch_bounds__(kPThreads, 1)
           break;
         }
         unsigned char* st = sm + s * kStageBytes;
-        float4* ah = reinterpret_cast<float4*>(st);
-        float4* al = reinterpret_cast<float4*>(st + kTileBytes);
-        float4 xa[4];
+        // A: this thread's row (tensor-memory lane) of the 64-byte-swizzled raw tile -> head and tail
+        // into the stage's tensor-memory columns (16-byte chunk c of row r sits at c ^ ((r >> 1) & 3))
+        {
+          const float4* rowp = reinterpret_cast<const float4*>(st + row * 64);
+          float x[16], h[16], l[16];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (t + 128 * r < a_rows * 4) xa[r] = ah[t + 128 * r];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (t + 128 * r < a_rows * 4) {
-            const float4 h = head4(xa[r]);
-            ah[t + 128 * r] = h;
-            al[t + 128 * r] = tail4(xa[r], h);
+          for (int c = 0; c < 4; ++c) {
+            const float4 v = rowp[c ^ ((row >> 1) & 3)];
+            x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
           }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            h[e] = tf32_rn(x[e]);
+            l[e] = tf32_rn(x[e] - h[e]);
+          }
+          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + kACol + 32u * s;
+          tmem_st16(ta, h);
+          tmem_st16(ta + 16u, l);
+          tmem_wait_st();
+        }
         if (CONJ) {
           const int vstride = args.b_rows * 4;  // float4s between variants
           float4* b1h = reinterpret_cast<float4*>(st + 2 * kTileBytes);
-          float4* b1l = b1h + vstride;
-          float4* b2h = b1h + 2 * vstride;
+          float4* b2h = b1h + vstride;
+          float4* b1l = b1h + 2 * vstride;
           float4* b2l = b1h + 3 * vstride;
           float4 xb[4];
 #pragma unroll
@@ -437,6 +453,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_before();
         mbar_arrive(su32(&bar_ready[s]));
       }
     }
@@ -564,7 +581,9 @@ __device__ __forceinline__ void split_d(double x, float& h, float& l) {
 
 // Dense B operands of the orbital right-multiplies from the packed G(tau) blocks.  For family 0
 // B[n][k] = G[k][n] (the multiply D = X G), for family 1 B[n][k] = G[n][k] (D = X G^T).  Layout
-// [fam][t][w][variant][n][2 nao] floats, variants (conj B) head, tail, (i conj B) head, tail.
+// [fam][t][w][variant][n][2 nao] floats, variants (conj B) head, (i conj B) head, (conj B) tail,
+// (i conj B) tail: the two heads (and the two tails) form one 128-row B operand whose MMA writes
+// Re D and Im D side by side.
 __global__ void k_tc_g_operands(const double2* __restrict__ G, long long g_elems, const long long* __restrict__ g_off,
                                 const int* __restrict__ bstart, const int* __restrict__ bsize,
                                 const long long* __restrict__ bdoff, int nt, int nw, int nao, int fam0, int nfam,
@@ -590,9 +609,10 @@ __global__ void k_tc_g_operands(const double2* __restrict__ G, long long g_elems
     float h, l;
     float* base = out + (tw * 4) * per * 2 + (long long)n * 2 * nao + 2 * k;
     const long long vs = per * 2;
-    split_d(g.x, h, l); base[0] = h; base[vs] = l;  base[2 * vs + 1] = h; base[3 * vs + 1] = l;
-    split_d(-g.y, h, l); base[1] = h; base[vs + 1] = l;
-    split_d(g.y, h, l); base[2 * vs] = h; base[3 * vs] = l;
+    // variants in the order (conj B head, i conj B head, conj B tail, i conj B tail)
+    split_d(g.x, h, l); base[0] = h; base[2 * vs] = l;  base[vs + 1] = h; base[3 * vs + 1] = l;
+    split_d(-g.y, h, l); base[1] = h; base[2 * vs + 1] = l;
+    split_d(g.y, h, l); base[vs] = h; base[3 * vs] = l;
   }
 }
 
@@ -623,10 +643,10 @@ __global__ void k_tc_p_operands(const double2* __restrict__ P, long long p_elems
       split_d(c2, v[2], v[3]);
     }
     float* base = out + (ti * 4) * per + (long long)n * kp + x;
-    base[0] = v[0];
-    base[per] = v[1];
-    base[2 * per] = v[2];
-    base[3 * per] = v[3];
+    base[0] = v[0];        // conj B head
+    base[2 * per] = v[1];  // conj B tail
+    base[per] = v[2];      // i conj B head
+    base[3 * per] = v[3];  // i conj B tail
   }
 }
 
@@ -703,8 +723,6 @@ sgw_status make_map4(sgw_ctx* c, CUtensorMap* m, const void* base, long long kre
   return SGW_OK;
 }
 
-int round32(int n) { return (n + 31) & ~31; }
-
 constexpr int kMaxDev = 64;
 bool g_attr_done[2][2][kMaxDev] = {};
 int g_sms[kMaxDev] = {};
@@ -713,6 +731,7 @@ template <bool CONJ, bool DRAIN>
 sgw_status launch_gemm(sgw_ctx* c, const CUtensorMap& am, const CUtensorMap& bm, const TcJob* jobs, long long njobs,
                        const TcArgs& a, cudaStream_t st) {
   if (njobs <= 0) return SGW_OK;
+  if (a.b_rows != 64) return c->fail(SGW_ERR_ARG, "tensor-core launch: B tiles are 64 rows");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return c->fail(SGW_ERR_CUDA, "no current device");
   if (!g_attr_done[CONJ][DRAIN][dev]) {
@@ -940,21 +959,22 @@ static sgw_status build_p0(sgw_ctx* c) {
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
     T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size();
-    for (long long p = 0; p < np; ++p) {
-      const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
-      TcJob j{};
-      j.a_y = 0; j.a_z = (int)p; j.b_y = 0;
-      j.b_z = (int)(((long long)0 * nt + t) * nw + c->rep[k2]);
-      j.a_x = 0; j.b_x = 0; j.nslab = 1; j.nchunk = nch_o; j.a_dz = 0; j.b_dz = 0;
-      j.m_rows = rows; j.n_valid = nao; j.n_mma = round16(nao);
-      j.out_off = ((long long)tl * np + p) * rows * nao;
-      vg.push_back(j);
-      TcJob g = j;
-      g.a_z = (int)((long long)tl * np + p);
-      g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
-      g.out_off = p * nc * (long long)rows * nao + (long long)tl * nao * nao;  // X[p][Q][tl][i][j]
-      gvg.push_back(g);
-    }
+    for (long long p = 0; p < np; ++p)
+      for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
+        const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
+        TcJob j{};
+        j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
+        j.b_z = (int)(((long long)0 * nt + t) * nw + c->rep[k2]);
+        j.a_x = 0; j.b_x = 0; j.nslab = 1; j.nchunk = nch_o; j.a_dz = 0; j.b_dz = 0;
+        j.m_rows = rows; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
+        j.out_off = ((long long)tl * np + p) * rows * nao + (long long)n0 * nao;  // Z'[A][j][c], column j = n0 + n
+        vg.push_back(j);
+        TcJob g = j;
+        g.a_z = (int)((long long)tl * np + p);
+        g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
+        g.out_off = p * nc * (long long)rows * nao + (long long)tl * nao * nao + (long long)n0 * nao;  // X[p][Q][tl][i][j]
+        gvg.push_back(g);
+      }
   }
   // Gram units per tau chunk over the tau-interleaved X: rows (Q, tl) of each pair slab
   std::vector<int2> prp;
@@ -1037,13 +1057,15 @@ static sgw_status build_sigma(sgw_ctx* c) {
     T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size();
     for (long long p = 0; p < np; ++p) {
       const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
-      TcJob j{};
-      j.a_y = 0; j.a_z = (int)p; j.b_y = 0;
-      j.b_z = (int)((long long)t * nw + c->rep[k2]);
-      j.nslab = 1; j.nchunk = nch_o;
-      j.m_rows = rows_v; j.n_valid = nao; j.n_mma = round16(nao);
-      j.out_off = ((long long)tl * np + p) * vs;
-      svg.push_back(j);
+      for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
+        TcJob j{};
+        j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
+        j.b_z = (int)((long long)t * nw + c->rep[k2]);
+        j.nslab = 1; j.nchunk = nch_o;
+        j.m_rows = rows_v; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
+        j.out_off = ((long long)tl * np + p) * vs + (long long)n0 * naux;  // X1T[i][b][A], column b = n0 + n
+        svg.push_back(j);
+      }
       const int wq = c->rep[qindex(c, k1, k2)];
       for (int b : wblocks[wq]) {
         const int s = info[3 * b], nb = info[3 * b + 1], d = info[3 * b + 2];
@@ -1135,7 +1157,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   const long long rows = (long long)naux * nao;
   CKS(make_map(c, &mV, c->d_V32[0], 2 * nao, rows, np, 8LL * nao, vs * 8, 128));
   CKS(make_map(c, &mZ, Zp, 2 * nao, rows, (long long)nc * np, 8LL * nao, vs * 8, 128));
-  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, round32(nao)));
+  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, 64));
   // Gram operands: rows Q, contracted (i, j) re/im
   CUtensorMap mXg, mVg;
   CKS(make_map(c, &mXg, X, 2LL * nao * nao, (long long)naux * nc, np, 8LL * nao * nao, (long long)nc * vs * 8, 32));
@@ -1145,7 +1167,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     TcArgs a{};
     a.a_box = 128;
-    a.b_rows = round32(nao);
+    a.b_rows = 64;
     a.mtiles = T.mt_vg; a.mode = 1; a.Rs = nao; a.S1 = (long long)nao * nao; a.S2 = nao;
     a.alpha = make_float2(1.f, 0.f); a.out = Zp;
     // Z'[A][j][c] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
@@ -1205,7 +1227,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   CUtensorMap mVt, mG, mX1, mP, mX2g, mVtg;
   const long long rows_v = (long long)nao * naux;
   CKS(make_map(c, &mVt, c->d_V32[1], 2 * nao, rows_v, np, 8LL * nao, vs * 8, 128));
-  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, round32(nao)));
+  CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, 64));
   CKS(make_map(c, &mX1, X1, 2LL * naux, (long long)nao * nao, (long long)nc * np, 8LL * naux, vs * 8, 128));
   CKS(make_map4(c, &mP, Pop, T.pt_k, T.pt_rows, (long long)nc * T.ninst, 4LL * T.pt_k, 4LL * T.pt_k * T.pt_rows,
                 16LL * T.pt_k * T.pt_rows, 64));
@@ -1221,7 +1243,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     // X1T[i][b][A] = sum_a V[A][i][a] G^{k2}(tau)[a][b]
     TcArgs a{};
     a.a_box = 128;
-    a.b_rows = round32(nao);
+    a.b_rows = 64;
     a.mtiles = T.mt_svg; a.mode = 1; a.Rs = naux; a.S1 = (long long)nao * naux; a.S2 = naux;
     a.alpha = make_float2(1.f, 0.f); a.out = X1;
     run(c, "sigma_vg_tc", T.fl_svg * ntc, 1, st, [&] {
