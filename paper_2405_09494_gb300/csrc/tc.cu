@@ -770,7 +770,7 @@ long long al256(long long bytes) { return (bytes + 255) & ~255LL; }
 // Contraction chunks per split-K unit (a unit's FP32 partial tile is added to the others in FP64).
 long long kchunk_target(bool drained) {
   const char* s = std::getenv(drained ? "SGW_TC_KCHUNK" : "SGW_TC_KCHUNK_UNDRAINED");
-  long long v = s ? std::atoll(s) : (drained ? 128 : 16);
+  long long v = s ? std::atoll(s) : (drained ? 256 : 16);
   return std::max(1LL, v);
 }
 
