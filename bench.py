@@ -314,7 +314,7 @@ def _mixed_errors(plain, mixed, state):
         H = sess.hartree_fock(G)
         Gn, mun = sess.dyson(S, H, mu, True)
         E = sess.energy(Gn, H, S)
-        return dict(P0=P0, P=P, Sigma=S, G=Gn), mun, E
+        return dict(P0=P0, P=P, Sigma=S, HF=H, G=Gn), mun, E
 
     a, mua, Ea = run(plain)
     b, mub, Eb = run(mixed)

@@ -312,6 +312,10 @@ extern "C" SGW_API sgw_status sgw_sync(sgw_ctx* c, sgw_stream stream) {
     cudaMemset(c->d_status, 0, sizeof(int));
     return c->fail(SGW_ERR_SINGULAR, "zero pivot in a block inversion");
   }
+  if (st == DEV_BADJOB) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    return c->fail(SGW_ERR_STATE, "a tensor-core job table entry failed its launch checks; results are invalid");
+  }
   if (st == DEV_TIMEOUT) {
     cudaMemset(c->d_status, 0, sizeof(int));
     return c->fail(SGW_ERR_TIMEOUT, "a tensor-core pipeline wait ran out of time; its results are invalid");

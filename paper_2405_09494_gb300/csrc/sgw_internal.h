@@ -15,7 +15,7 @@ namespace sgw {
 using cplx = std::complex<double>;
 
 // Status codes written by kernels into the context's device status word.
-enum DeviceStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2 };
+enum DeviceStatus : int { DEV_OK = 0, DEV_SINGULAR = 1, DEV_TIMEOUT = 2, DEV_BADJOB = 3 };
 
 // One block-diagonal partition of an index range [0, n): for every index v,
 // the first index and size of its block and the offset of the block's data

@@ -306,6 +306,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int abox = args.a_box;
         const int a_boxes = (ui.m_valid + abox - 1) / abox;
         const uint32_t tx_bytes = (uint32_t)(a_boxes * abox * 64) + (uint32_t)(args.b_rows * 64 * (CONJ ? 1 : 4));
+        // the job must describe copies that start on 16-byte boundaries and fit the stage; otherwise
+        // nothing is issued, the status records it and the CTA stops
+        if (abox <= 0 || 128 % abox != 0 || a_boxes * abox > 128 || args.b_rows != 64 || (job.a_x & 3) ||
+            (job.b_x & 3) || job.nchunk < 1 || job.nslab < 1 || job.a_y < 0 || job.b_y < 0) {
+          atomicExch(status, (int)DEV_BADJOB);
+          abort_flag = 1;
+          break;
+        }
         bool ok = true;
         for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
           const int s = (int)(gk % kPStages);

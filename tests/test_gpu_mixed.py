@@ -56,6 +56,7 @@ def mixed_t1(request):
         P0=rel_err(to_np(sess.unfold(1, lP0)), P0),
         P=rel_err(to_np(sess.unfold(1, lP)), P),
         Sigma=rel_err(to_np(sess.unfold(0, lSig)), Sig),
+        HF=rel_err(to_np(sess.unfold(0, lShf))[:, 0], Shf),  # one matrix per k: drop the series axis
         G=rel_err(to_np(sess.unfold(0, lG1)), G1),
         mu=abs(lmu1 - mu1),
         E=abs(lE[0] - E[0].real) / max(1.0, abs(E[0])),
@@ -67,7 +68,7 @@ def mixed_t1(request):
     return out
 
 
-@pytest.mark.parametrize("q", ["P0", "P", "Sigma", "G", "E"])
+@pytest.mark.parametrize("q", ["P0", "P", "Sigma", "HF", "G", "E"])
 def test_mixed_form_error_per_quantity(mixed_t1, q):
     assert mixed_t1[q] < TOL, (q, mixed_t1[q])
 
