@@ -97,6 +97,12 @@ CONFIGS = {
         name="c4", index=3, structure="diamond", nk=(4, 4, 4), ao_shells=_shells({0: 4, 1: 4, 2: 2}),
         aux_shells=_shells({0: 10, 1: 10, 2: 11, 3: 4, 4: 3}), ntau=150, beta=200.0, mats_f=F150, mats_b=B150,
         description="diamond Fd-3m (non-symmorphic), 4x4x4 mesh (8 wedge points), nao 52, naux 300, 150 tau, beta 200"),
+    "c5": Config(
+        name="c5", index=4, structure="rocksalt", nk=(4, 4, 4), ao_shells=_shells({0: 7, 1: 6, 2: 4, 3: 1}),
+        aux_shells=_shells({0: 20, 1: 20, 2: 22, 3: 8, 4: 6}), ntau=200, beta=500.0, mats_f=[], mats_b=[],
+        damping=0.5,
+        description="rocksalt Oh, 4x4x4 mesh (8 wedge points), nao 104, naux 600, 200 tau, beta 500, "
+                    "self-consistent loop with damping 0.5"),
     # small rocksalt cell for the smoke run and the fast parity tests: 2x2x2 mesh (3 wedge points)
     "t1": Config(
         name="t1", index=10, structure="rocksalt", nk=(2, 2, 2), ao_shells=(0, 1), aux_shells=(0, 0, 1, 2),

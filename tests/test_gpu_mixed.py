@@ -109,10 +109,12 @@ def _chain_errors(cfg):
     return out, kernels
 
 
-@pytest.mark.parametrize("case", ["one_block_160", "diamond_2"])
+@pytest.mark.parametrize("case", ["one_block_160", "diamond_2", "nao_72"])
 def test_mixed_chains_on_large_and_nonsymmorphic_blocks(case):
-    """Auxiliary blocks above one 128-row tile (several M and N tiles per block) and the
-    non-symmorphic diamond group (odd block starts, fractional translations)."""
+    """Auxiliary blocks above one 128-row tile (several M and N tiles per block), the
+    non-symmorphic diamond group (odd block starts, fractional translations), and more than 64
+    orbitals (two output-column tiles in the orbital multiplies and in the Sigma Gram, blocks
+    that straddle them)."""
     import dataclasses
 
     torch = pytest.importorskip("torch")
@@ -124,6 +126,9 @@ def test_mixed_chains_on_large_and_nonsymmorphic_blocks(case):
     if case == "one_block_160":
         cfg = dataclasses.replace(base, name="none-160", structure="none", nk=(1, 1, 2), ao_shells=(0,) * 8,
                                   aux_shells=(0,) * 160)
+    elif case == "nao_72":
+        cfg = dataclasses.replace(base, name="none-72", structure="none", nk=(1, 1, 2), ao_shells=(0,) * 72,
+                                  aux_shells=(0,) * 40)
     else:
         cfg = dataclasses.replace(base, name="diamond-2", index=3, structure="diamond")
     errs, kernels = _chain_errors(cfg)
