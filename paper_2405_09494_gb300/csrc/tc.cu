@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -68,6 +69,8 @@ struct TcArgs {
 // Cached jobs of the tensor-core chains.
 struct TcPlan {
   bool built_p0 = false, built_sigma = false;
+  long long unit_p0 = 0, unit_s = 0;   // split-K unit length of the Gram reductions (chunks)
+  bool tuned_p0 = false, tuned_s = false;
   int nc_p0 = 0, nc_s = 0;
   std::vector<long long> vg_start, gvg_start, pg_start, pr_start;            // per tau: first job / unit / tile
   std::vector<long long> svg_start, pvg_start, sg_start, sr_start;
@@ -775,11 +778,17 @@ void fr(T*& p) {
 int round16(int n) { return (n + 15) & ~15; }
 long long al256(long long bytes) { return (bytes + 255) & ~255LL; }
 
-// Contraction chunks per split-K unit (a unit's FP32 partial tile is added to the others in FP64).
-long long kchunk_target(bool drained) {
-  const char* s = std::getenv(drained ? "SGW_TC_KCHUNK" : "SGW_TC_KCHUNK_UNDRAINED");
-  long long v = s ? std::atoll(s) : (drained ? 256 : 16);
-  return std::max(1LL, v);
+// Split-K unit length of the Gram reductions (chunks of 16 reals): an environment value fixes it,
+// otherwise the autotuner picks one of kUnitCandidates on the first call of a context.
+constexpr long long kUnitDefault = 256;
+constexpr long long kUnitCandidates[] = {128, 256, 512};
+long long unit_override() {
+  const char* s = std::getenv("SGW_TC_KCHUNK");
+  return s ? std::max(1LL, std::atoll(s)) : 0;
+}
+bool autotune_enabled() {
+  const char* s = std::getenv("SGW_TC_AUTOTUNE");
+  return unit_override() == 0 && !(s && std::strcmp(s, "0") == 0);
 }
 
 struct KRange {
@@ -811,13 +820,13 @@ struct GramTiles {
   int mts, nts, rpt, ntile;
 };
 GramTiles gram_interleaved(std::vector<TcJob>& jobs, long long slot0, long long slot, const TcJob& proto, int r0,
-                           int nr, int nc, int ncols, int ntile, int nslab, int nchunk) {
+                           int nr, int nc, int ncols, int ntile, int nslab, int nchunk, long long unit) {
   GramTiles g;
   g.rpt = 128 / nc;
   g.ntile = ntile;
   g.mts = (nr + g.rpt - 1) / g.rpt;
   g.nts = (ncols + ntile - 1) / ntile;
-  const std::vector<KRange> kr = split_k(nslab, nchunk, kchunk_target(true));
+  const std::vector<KRange> kr = split_k(nslab, nchunk, unit);
   g.first = (long long)jobs.size() - slot0;
   g.count = (int)kr.size();
   g.stride = g.mts * g.nts;
@@ -949,6 +958,47 @@ void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long
   }
 }
 
+// Gram jobs of P0 for split-K units of `unit` chunks (replaces the previous tables).
+static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
+  TcPlan& T = *c->tc;
+  const int Nk = c->Nk, nt = c->nt, nao = c->nao, nc = T.nc_p0;
+  const long long np = (long long)c->nwedge * Nk;
+  const int nch_g = (2 * nao * nao + 15) / 16;
+  std::vector<TcJob> pg;
+  std::vector<TcTile> pr;
+  T.pg_start.assign(nt + 1, 0); T.pr_start.assign(nt + 1, 0);
+  // Gram units per tau chunk over the tau-interleaved X: rows (Q, tl) of each pair slab
+  std::vector<int2> prp;
+  T.prp_start.assign(nt + 1, 0);
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long slot0 = (long long)pg.size(), tile0 = (long long)pr.size();
+    for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); T.prp_start[t] = prp.size(); }
+    for (size_t b = 0; b < c->auxb_off.size(); ++b) {
+      const int w = c->auxb_w[b], nb = c->auxb_n[b], s = c->auxb_start[b];
+      TcJob j{};
+      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
+      j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
+      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit);
+      for (int t = t0; t < t1; ++t)
+        gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
+    }
+    reduce_pieces(pr, tile0, (long long)pr.size(), prp);
+  }
+  T.prp_start[nt] = prp.size();
+  CKS(up(c, T.d_prp, prp));
+  T.pg_start[nt] = pg.size(); T.pr_start[nt] = pr.size();
+  T.max_units_p0 = 0;
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    T.max_units_p0 = std::max(T.max_units_p0, T.pg_start[t1] - T.pg_start[t0]);
+  }
+  (void)np;
+  CKS(up(c, T.d_pg, pg));
+  CKS(up(c, T.d_pr, pr));
+  return SGW_OK;
+}
+
 static sgw_status build_p0(sgw_ctx* c) {
   TcPlan& T = *c->tc;
   if (T.built_p0) return SGW_OK;
@@ -959,11 +1009,9 @@ static sgw_status build_p0(sgw_ctx* c) {
   T.nc_p0 = nc;
   const int rows = naux * nao;
   T.mt_vg = (rows + 127) / 128;
-  std::vector<TcJob> vg, gvg, pg;
-  std::vector<TcTile> pr;
-  T.vg_start.assign(nt + 1, 0); T.gvg_start.assign(nt + 1, 0); T.pg_start.assign(nt + 1, 0); T.pr_start.assign(nt + 1, 0);
-  const int kq = 2 * nao * nao;
-  const int nch_g = (kq + 15) / 16, nch_o = (2 * nao + 15) / 16;
+  std::vector<TcJob> vg, gvg;
+  T.vg_start.assign(nt + 1, 0); T.gvg_start.assign(nt + 1, 0);
+  const int nch_o = (2 * nao + 15) / 16;
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
     T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size();
@@ -984,32 +1032,9 @@ static sgw_status build_p0(sgw_ctx* c) {
         gvg.push_back(g);
       }
   }
-  // Gram units per tau chunk over the tau-interleaved X: rows (Q, tl) of each pair slab
-  std::vector<int2> prp;
-  T.prp_start.assign(nt + 1, 0);
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
-    const long long slot0 = (long long)pg.size(), tile0 = (long long)pr.size();
-    for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); T.prp_start[t] = prp.size(); }
-    for (size_t b = 0; b < c->auxb_off.size(); ++b) {
-      const int w = c->auxb_w[b], nb = c->auxb_n[b], s = c->auxb_start[b];
-      TcJob j{};
-      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
-      j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g);
-      for (int t = t0; t < t1; ++t)
-        gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
-    }
-    reduce_pieces(pr, tile0, (long long)pr.size(), prp);
-  }
-  T.prp_start[nt] = prp.size();
-  CKS(up(c, T.d_prp, prp));
-  T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size(); T.pg_start[nt] = pg.size(); T.pr_start[nt] = pr.size();
-  T.max_units_p0 = 0;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
-    T.max_units_p0 = std::max(T.max_units_p0, T.pg_start[t1] - T.pg_start[t0]);
-  }
+  T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size();
+  T.unit_p0 = unit_override() ? unit_override() : kUnitDefault;
+  CKS(build_p0_gram(c, T.unit_p0));
   T.fl_vg = T.fl_gvg = T.fl_pg = 0;
   for (long long p = 0; p < np; ++p) {
     T.fl_vg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
@@ -1018,9 +1043,50 @@ static sgw_status build_p0(sgw_ctx* c) {
   for (int w = 0; w < nw; ++w) T.fl_pg += 8.0 * Nk * (double)nao * nao * c->part_aux[w].elems;
   CKS(up(c, T.d_vg, vg));
   CKS(up(c, T.d_gvg, gvg));
-  CKS(up(c, T.d_pg, pg));
-  CKS(up(c, T.d_pr, pr));
   T.built_p0 = true;
+  return SGW_OK;
+}
+
+// Gram jobs of Sigma~ for split-K units of `unit` chunks (replaces the previous tables).
+static sgw_status build_sigma_gram(sgw_ctx* c, long long unit) {
+  TcPlan& T = *c->tc;
+  const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux, nc = T.nc_s;
+  const int nch_g = (2 * naux * nao + 15) / 16;
+  std::vector<TcJob> sg;
+  std::vector<TcTile> sr;
+  T.sg_start.assign(nt + 1, 0); T.sr_start.assign(nt + 1, 0);
+  // Gram units per tau chunk: the whole nao x nao matrix per wedge point over the tau-interleaved X2
+  // (rows (i, tl)); the reduction picks the diagonal blocks out of the partial tiles
+  std::vector<int2> srp;
+  T.srp_start.assign(nt + 1, 0);
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long slot0 = (long long)sg.size(), tile0 = (long long)sr.size();
+    for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); T.srp_start[t] = srp.size(); }
+    for (int w = 0; w < nw; ++w) {
+      TcJob j{};
+      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
+      j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
+      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g, unit);
+      for (int t = t0; t < t1; ++t)
+        for (size_t b = 0; b < c->aob_off.size(); ++b) {
+          if (c->aob_w[b] != w) continue;
+          const int nb = c->aob_n[b], s = c->aob_start[b];
+          gram_out_tiles(sr, g, 0, nc, t - t0, s, nb, 0, s, nb, (long long)t * c->g_elems + c->aob_off[b], nb);
+        }
+    }
+    reduce_pieces(sr, tile0, (long long)sr.size(), srp);
+  }
+  T.srp_start[nt] = srp.size();
+  CKS(up(c, T.d_srp, srp));
+  T.sg_start[nt] = sg.size(); T.sr_start[nt] = sr.size();
+  T.max_units_s = 0;
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    T.max_units_s = std::max(T.max_units_s, T.sg_start[t1] - T.sg_start[t0]);
+  }
+  CKS(up(c, T.d_sg, sg));
+  CKS(up(c, T.d_sr, sr));
   return SGW_OK;
 }
 
@@ -1056,10 +1122,9 @@ static sgw_status build_sigma(sgw_ctx* c) {
   const int rows_v = nao * naux, rows_x = nao * nao;
   T.mt_svg = (rows_v + 127) / 128;
   T.mt_pvg = (rows_x + 127) / 128;
-  std::vector<TcJob> svg, pvg, sg;
-  std::vector<TcTile> sr;
-  T.svg_start.assign(nt + 1, 0); T.pvg_start.assign(nt + 1, 0); T.sg_start.assign(nt + 1, 0); T.sr_start.assign(nt + 1, 0);
-  const int nch_o = (2 * nao + 15) / 16, kg = 2 * naux * nao, nch_g = (kg + 15) / 16;
+  std::vector<TcJob> svg, pvg;
+  T.svg_start.assign(nt + 1, 0); T.pvg_start.assign(nt + 1, 0);
+  const int nch_o = (2 * nao + 15) / 16;
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
     T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size();
@@ -1091,36 +1156,9 @@ static sgw_status build_sigma(sgw_ctx* c) {
       }
     }
   }
-  // Gram units per tau chunk: the whole nao x nao matrix per wedge point over the tau-interleaved X2
-  // (rows (i, tl)); the reduction picks the diagonal blocks out of the partial tiles
-  std::vector<int2> srp;
-  T.srp_start.assign(nt + 1, 0);
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
-    const long long slot0 = (long long)sg.size(), tile0 = (long long)sr.size();
-    for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); T.srp_start[t] = srp.size(); }
-    for (int w = 0; w < nw; ++w) {
-      TcJob j{};
-      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
-      j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g);
-      for (int t = t0; t < t1; ++t)
-        for (size_t b = 0; b < c->aob_off.size(); ++b) {
-          if (c->aob_w[b] != w) continue;
-          const int nb = c->aob_n[b], s = c->aob_start[b];
-          gram_out_tiles(sr, g, 0, nc, t - t0, s, nb, 0, s, nb, (long long)t * c->g_elems + c->aob_off[b], nb);
-        }
-    }
-    reduce_pieces(sr, tile0, (long long)sr.size(), srp);
-  }
-  T.srp_start[nt] = srp.size();
-  CKS(up(c, T.d_srp, srp));
-  T.svg_start[nt] = svg.size(); T.pvg_start[nt] = pvg.size(); T.sg_start[nt] = sg.size(); T.sr_start[nt] = sr.size();
-  T.max_units_s = 0;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
-    T.max_units_s = std::max(T.max_units_s, T.sg_start[t1] - T.sg_start[t0]);
-  }
+  T.svg_start[nt] = svg.size(); T.pvg_start[nt] = pvg.size();
+  T.unit_s = unit_override() ? unit_override() : kUnitDefault;
+  CKS(build_sigma_gram(c, T.unit_s));
   T.fl_svg = T.fl_pvg = T.fl_sg = 0;
   for (long long p = 0; p < np; ++p) {
     const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
@@ -1130,14 +1168,53 @@ static sgw_status build_sigma(sgw_ctx* c) {
   for (int w = 0; w < nw; ++w) T.fl_sg += 8.0 * Nk * (double)naux * nao * c->part_ao[w].elems;
   CKS(up(c, T.d_svg, svg));
   CKS(up(c, T.d_pvg, pvg));
-  CKS(up(c, T.d_sg, sg));
-  CKS(up(c, T.d_sr, sr));
   T.built_sigma = true;
   return SGW_OK;
 }
 
 static sgw_status ensure_plan(sgw_ctx* c) {
   if (!c->tc) c->tc = new TcPlan();
+  return SGW_OK;
+}
+
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+// Autotuner of the split-K unit length of a Gram reduction: build the jobs for each candidate,
+// time the launch of the first tau chunk (Gram + FP64 sum of the partial tiles, second of two
+// runs, CUDA events on the launching stream) and keep the fastest.  Runs once per context, on
+// the first call outside a stream capture.
+template <class Build, class Launch>
+static sgw_status tune_unit(sgw_ctx* c, cudaStream_t st, const char* what, long long& unit, Build&& build,
+                            Launch&& launch) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return c->fail(SGW_ERR_CUDA, "autotuner events");
+  long long best_unit = unit;
+  float best = 1e30f;
+  for (long long cand : kUnitCandidates) {
+    CKS(build(cand));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(a, st);
+      CKS(launch());
+      cudaEventRecord(b, st);
+      if (cudaEventSynchronize(b) != cudaSuccess) return c->fail(SGW_ERR_CUDA, "autotuner timing");
+      cudaEventElapsedTime(&ms, a, b);
+    }
+    if (ms < best) {
+      best = ms;
+      best_unit = cand;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  unit = best_unit;
+  CKS(build(unit));
+  const char* v = std::getenv("SGW_VERBOSE");
+  if (v && v[0] == '1') std::fprintf(stderr, "sgw autotune: %s split-K unit %lld chunks (%.3f ms)\n", what, unit, best);
   return SGW_OK;
 }
 
@@ -1149,8 +1226,17 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   const long long np = (long long)nw * Nk, vs = (long long)naux * nao * nao;
   const long long inter = (long long)nc * np * vs;  // complex64 elements
   const long long gop = 2LL * nt * nw * 4 * nao * 2 * nao;  // floats
+  const bool tune = !T.tuned_p0 && autotune_enabled() && !capturing(st);
+  long long max_units = T.max_units_p0;
+  if (tune) {  // partial tiles for the candidate with the most units
+    for (long long cand : kUnitCandidates) {
+      CKS(build_p0_gram(c, cand));
+      max_units = std::max(max_units, T.max_units_p0);
+    }
+    CKS(build_p0_gram(c, T.unit_p0));
+  }
   const long long b_z = al256(inter * 8), b_x = al256(inter * 8), b_g = al256(gop * 4),
-                  b_p = al256(T.max_units_p0 * kSlotD * 8);
+                  b_p = al256(max_units * kSlotD * 8);
   CKS(ensure_workspace(c, (size_t)(b_z + b_x + b_g + b_p)));
   unsigned char* ws = reinterpret_cast<unsigned char*>(c->d_ws);
   float2* Zp = reinterpret_cast<float2*>(ws);
@@ -1196,17 +1282,29 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
     g.a_box = 32;
     g.b_rows = 64;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
-    run(c, "p0_gram_tc", T.fl_pg * ntc, 1, st, [&] {
-      s3 = launch_gemm<true, true>(c, mXg, mVg, T.d_pg + T.pg_start[t0], T.pg_start[t1] - T.pg_start[t0], g, st);
-    });
-    CKS(s3);
-    const long long r0 = T.pr_start[t0], q0 = T.prp_start[t0], q1 = T.prp_start[t1];
-    run(c, "gram_reduce", 0.0, 1, st, [&] {
+    auto gemm = [&]() {
+      return launch_gemm<true, true>(c, mXg, mVg, T.d_pg + T.pg_start[t0], T.pg_start[t1] - T.pg_start[t0], g, st);
+    };
+    auto reduce = [&]() {
+      const long long r0 = T.pr_start[t0], q0 = T.prp_start[t0], q1 = T.prp_start[t1];
       if (q1 > q0)
         k_tc_reduce<<<(unsigned)(q1 - q0), 256, 0, st>>>(T.d_pr + r0, T.d_prp + q0, part, out, make_double2(alpha, 0.0),
                                                          kSlotD);
-    });
+    };
+    if (tune && t0 == 0) {
+      auto both = [&]() -> sgw_status {
+        CKS(gemm());
+        reduce();
+        return SGW_OK;
+      };
+      CKS(tune_unit(c, st, "P0", T.unit_p0, [&](long long u) { return build_p0_gram(c, u); }, both));
+      T.tuned_p0 = true;
+    }
+    run(c, "p0_gram_tc", T.fl_pg * ntc, 1, st, [&] { s3 = gemm(); });
+    CKS(s3);
+    run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
+  if (tune) T.tuned_p0 = true;
   return SGW_OK;
 }
 
@@ -1219,8 +1317,17 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   const long long inter = (long long)nc * np * vs;
   const long long gop = 1LL * nt * nw * 4 * nao * 2 * nao;
   const long long pop = (long long)nc * T.ninst * 4 * T.pt_rows * T.pt_k;
+  const bool tune = !T.tuned_s && autotune_enabled() && !capturing(st);
+  long long max_units = T.max_units_s;
+  if (tune) {  // partial tiles for the candidate with the most units
+    for (long long cand : kUnitCandidates) {
+      CKS(build_sigma_gram(c, cand));
+      max_units = std::max(max_units, T.max_units_s);
+    }
+    CKS(build_sigma_gram(c, T.unit_s));
+  }
   const long long b_1 = al256(inter * 8), b_2 = al256(inter * 8), b_g = al256(gop * 4), b_pp = al256(pop * 4),
-                  b_p = al256(T.max_units_s * T.slot_s * 8);
+                  b_p = al256(max_units * T.slot_s * 8);
   CKS(ensure_workspace(c, (size_t)(b_1 + b_2 + b_g + b_pp + b_p)));
   unsigned char* ws = reinterpret_cast<unsigned char*>(c->d_ws);
   float2* X1 = reinterpret_cast<float2*>(ws);
@@ -1273,17 +1380,29 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     g.a_box = 32;
     g.b_rows = 64;
     g.mtiles = 1; g.mode = 0; g.Rs = 1; g.alpha = make_float2(1.f, 0.f); g.out = part;
-    run(c, "sigma_gram_tc", T.fl_sg * ntc, 1, st, [&] {
-      s3 = launch_gemm<true, true>(c, mX2g, mVtg, T.d_sg + T.sg_start[t0], T.sg_start[t1] - T.sg_start[t0], g, st);
-    });
-    CKS(s3);
-    const long long r0 = T.sr_start[t0], q0 = T.srp_start[t0], q1 = T.srp_start[t1];
-    run(c, "gram_reduce", 0.0, 1, st, [&] {
+    auto gemm = [&]() {
+      return launch_gemm<true, true>(c, mX2g, mVtg, T.d_sg + T.sg_start[t0], T.sg_start[t1] - T.sg_start[t0], g, st);
+    };
+    auto reduce = [&]() {
+      const long long r0 = T.sr_start[t0], q0 = T.srp_start[t0], q1 = T.srp_start[t1];
       if (q1 > q0)
         k_tc_reduce<<<(unsigned)(q1 - q0), 256, 0, st>>>(T.d_sr + r0, T.d_srp + q0, part, out,
                                                          make_double2(-1.0 / c->Nk, 0.0), T.slot_s);
-    });
+    };
+    if (tune && t0 == 0) {
+      auto both = [&]() -> sgw_status {
+        CKS(gemm());
+        reduce();
+        return SGW_OK;
+      };
+      CKS(tune_unit(c, st, "Sigma", T.unit_s, [&](long long u) { return build_sigma_gram(c, u); }, both));
+      T.tuned_s = true;
+    }
+    run(c, "sigma_gram_tc", T.fl_sg * ntc, 1, st, [&] { s3 = gemm(); });
+    CKS(s3);
+    run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
+  if (tune) T.tuned_s = true;
   return SGW_OK;
 }
 
