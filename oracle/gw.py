@@ -175,7 +175,7 @@ def g_minus_tau(G):
 # --------------------------------------------------------------------------
 # P0, P, Sigma
 # --------------------------------------------------------------------------
-def polarization(G, V, nk, s=2, loop_sign=+1, qs=None):
+def polarization(G, V, nk, s=2, loop_sign=+1, qs=None, pairs=None):
     """Bare bubble P0^q_{QQ'}(tau) of Eq. (P0) for every q of the mesh.
 
     P0^q_{QQ'}(tau) = loop_sign (s/N_k) sum_k sum_{abcd}
@@ -184,7 +184,9 @@ def polarization(G, V, nk, s=2, loop_sign=+1, qs=None):
         X1(Q)_{ca}  = sum_d G^k_{cd}(-tau) V^{k,k+q}_{da}(Q),
         X2(Q')_{ac} = sum_b G^{k+q}_{ab}(tau) V^{k+q,k}_{bc}(Q'),
         P0_{QQ'}   += sum_{ca} X1(Q)_{ca} X2(Q')_{ac}.
-    ``qs`` restricts the evaluation to a list of q (other entries stay zero).
+    ``qs`` restricts the evaluation to a list of q (other entries stay zero); ``pairs``, a set
+    of (k, k + q), to the terms of those pairs (a partial sum over k, as one rank of a partition
+    of the pairs computes it).
     """
     Vf = as_vfun(V)
     Nk, nt, nao, _ = G.shape
@@ -194,6 +196,8 @@ def polarization(G, V, nk, s=2, loop_sign=+1, qs=None):
     for q in (range(Nk) if qs is None else qs):
         for k in range(Nk):
             kq = kadd(nk, k, q)
+            if pairs is not None and (k, kq) not in pairs:
+                continue
             Vkq = Vf(k, kq)  # [Q][d][a]
             Vqk = Vf(kq, k)  # [Q'][b][c]
             # X1[t][c][Q][a] = sum_d G^k(-tau)[t][c][d] V^{k,k+q}[Q][d][a]   (one GEMM over all t, Q)
@@ -228,7 +232,7 @@ def screened_interaction(P0_tau, TB, TBbar):
     return to_matsubara(Pw, TBbar), P0w, Pw
 
 
-def self_energy(G, P, V, nk, ks=None):
+def self_energy(G, P, V, nk, ks=None, pairs=None):
     """Dynamic GW self-energy of Eq. (sigma) for every k of the mesh.
 
     Sigma^k_ij(tau) = -(1/N_k) sum_q sum_ab sum_QQ'
@@ -237,7 +241,8 @@ def self_energy(G, P, V, nk, ks=None):
         X1(Q)_{ib}  = sum_a V^{k,k-q}_{ia}(Q) G^{k-q}_{ab}(tau),
         X2(Q')_{ib} = sum_Q X1(Q)_{ib} P^q_{QQ'}(tau),
         Sigma_ij   += sum_{Q' b} X2(Q')_{ib} V^{k-q,k}_{bj}(Q').
-    ``ks`` restricts the evaluation to a list of k (other entries stay zero).
+    ``ks`` restricts the evaluation to a list of k (other entries stay zero); ``pairs``, a set
+    of (k, k - q), to the terms of those pairs (a partial sum over q).
     """
     Vf = as_vfun(V)
     Nk, nt, nao, _ = G.shape
@@ -246,6 +251,8 @@ def self_energy(G, P, V, nk, ks=None):
     for k in (range(Nk) if ks is None else ks):
         for q in range(Nk):
             kmq = ksub(nk, k, q)
+            if pairs is not None and (k, kmq) not in pairs:
+                continue
             V1 = Vf(k, kmq)  # [Q][i][a]
             V2 = Vf(kmq, k)  # [Q'][b][j]
             # X1[Q][i][t][b] = sum_a V^{k,k-q}[Q][i][a] G^{k-q}(tau)[t][a][b]   (one GEMM over all Q, t)
