@@ -316,13 +316,21 @@ def particle_number(gamma, S, s=2):
 
 
 def dyson(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, n_elec=None, s=2, search_mu=False,
-          mu_lo=-20.0, mu_hi=20.0, n_tol=1e-11, max_bisect=64):
+          mu_lo=-20.0, mu_hi=20.0, n_tol=1e-11, max_trials=64):
     """G(tau) from Eq. (dyson), optionally with the chemical-potential search.
 
     Sigma~(i w) = TF Sigma~(tau); G(i w) by inversion; G(tau) = TFbar G(i w).
-    With search_mu, mu is found by bisection on [mu_lo, mu_hi] so that the
-    particle number of gamma = -G(beta^-) equals N_e: stop when
-    |N(mu) - N_e| <= n_tol or after max_bisect halvings (reading C-7).
+    With search_mu, mu solves N(mu) = N_e, N the particle number of gamma = -G(beta^-)
+    (reading C-7), by Newton's method kept inside a bracket, starting from the given mu:
+      * a trial at mu gives r = N(mu) - N_e and N'(mu); stop when |r| <= n_tol;
+      * the bracket [mu_lo, mu_hi] shrinks to the side of mu that keeps the root
+        (N increases with mu: r > 0 moves the upper end to mu, else the lower end);
+      * the next trial is the Newton point mu - r / N'(mu) when N' > 0, the point lies
+        strictly inside the bracket and |r| is at most half the previous trial's |r|;
+        otherwise the bracket's midpoint;
+      * after max_trials trials the next point is taken as it stands.
+    N'(mu) follows from differentiating Eq. (dyson): dG(i w)/dmu = -G(i w) S G(i w).
+    A start outside the open bracket starts at its midpoint.
     """
     TF, TFbar, nu_f = grid_ops["TF"], grid_ops["TFbar"], grid_ops["nu_f"]
     Sigma_w = to_matsubara(Sigma_tau, TF)
@@ -332,22 +340,43 @@ def dyson(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, n_elec=None, s=2, search_mu=
     def number(mu_):
         Gw = dyson_matsubara(H0, S, Sigma_hf, Sigma_w, mu_, nu_f)
         gam = np.einsum("m,kmij->kij", wgt, Gw)
-        return particle_number(gam, S, s), Gw
+        dgam = -np.einsum("m,kmij,kjl,kmlp->kip", wgt, Gw, S, Gw)
+        return particle_number(gam, S, s), particle_number(dgam, S, s), Gw
 
     if search_mu:
         lo, hi = mu_lo, mu_hi
-        for _ in range(max_bisect):
-            mid = 0.5 * (lo + hi)
-            n, _ = number(mid)
-            if abs(n - n_elec) <= n_tol:
+        if not (lo < mu < hi):
+            mu = 0.5 * (lo + hi)
+        r_prev = np.inf
+        for _ in range(max_trials):
+            n, dn, _ = number(mu)
+            res = n - n_elec
+            if abs(res) <= n_tol:
                 break
-            if n > n_elec:
-                hi = mid
+            if res > 0:
+                hi = mu
             else:
-                lo = mid
-        mu = mid
-    _, Gw = number(mu)
+                lo = mu
+            newton = mu - res / dn if dn > 0 else np.nan
+            if lo < newton < hi and abs(res) <= 0.5 * r_prev:
+                nxt = newton
+            else:
+                nxt = 0.5 * (lo + hi)
+            r_prev = abs(res)
+            mu = nxt
+    _, _, Gw = number(mu)
     return to_matsubara(Gw, TFbar), mu
+
+
+def particle_number_and_slope(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, s=2):
+    """(N(mu), N'(mu)) as the search of :func:`dyson` evaluates them (for pins)."""
+    TF, TFbar, nu_f = grid_ops["TF"], grid_ops["TFbar"], grid_ops["nu_f"]
+    Sigma_w = to_matsubara(Sigma_tau, TF)
+    wgt = -(grid.value_at_beta_minus(TF.shape[1]) @ TFbar)
+    Gw = dyson_matsubara(H0, S, Sigma_hf, Sigma_w, mu, nu_f)
+    gam = np.einsum("m,kmij->kij", wgt, Gw)
+    dgam = -np.einsum("m,kmij,kjl,kmlp->kip", wgt, Gw, S, Gw)
+    return particle_number(gam, S, s), particle_number(dgam, S, s)
 
 
 def energy(H0, S, G_tau, Sigma_hf, Sigma_tau, beta, s=2):

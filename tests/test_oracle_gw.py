@@ -73,6 +73,51 @@ def test_dyson_without_self_energy_is_g0(small):
     assert abs(mu_s - small["mu"]) < 1e-8
 
 
+def _interacting_sigma(small, scale=0.05, seed=5):
+    """A Hermitian, tau-even self-energy pair (Sigma_HF, Sigma~(tau)) to make the Dyson step non-trivial."""
+    rng = np.random.default_rng(seed)
+    Nk, n = small["H"].shape[0], small["n"]
+    X = rng.normal(size=(Nk, 3, 3)) + 1j * rng.normal(size=(Nk, 3, 3))
+    Shf = scale * (X + X.conj().transpose(0, 2, 1))
+    Y = rng.normal(size=(Nk, 1, 3, 3)) + 1j * rng.normal(size=(Nk, 1, 3, 3))
+    Y = Y + Y.conj().transpose(0, 1, 3, 2)
+    tau = small["ops"]["tau"]
+    shape = np.exp(-3.0 * tau / small["beta"]) + np.exp(-3.0 * (small["beta"] - tau) / small["beta"])
+    return Shf, -scale * shape[None, :, None, None] * Y
+
+
+def test_particle_number_slope_is_the_derivative(small):
+    H, S, ops = small["H"], small["S"], small["ops"]
+    Shf, Sig = _interacting_sigma(small)
+    for mu in (-0.3, 0.1, 0.4):
+        n, dn = gw.particle_number_and_slope(H, S, Shf, Sig, mu, ops)
+        h = 1e-5
+        fd = (gw.particle_number_and_slope(H, S, Shf, Sig, mu + h, ops)[0]
+              - gw.particle_number_and_slope(H, S, Shf, Sig, mu - h, ops)[0]) / (2 * h)
+        assert dn > 0
+        assert abs(dn - fd) < 1e-6 * max(1.0, abs(fd)), (mu, dn, fd)
+
+
+def test_mu_search_finds_the_root_from_any_start(small):
+    H, S, ops = small["H"], small["S"], small["ops"]
+    Shf, Sig = _interacting_sigma(small)
+    # brute force: plain bisection on N(mu) to a width of 1e-14
+    lo, hi = -20.0, 20.0
+    while hi - lo > 1e-14:
+        mid = 0.5 * (lo + hi)
+        if gw.particle_number_and_slope(H, S, Shf, Sig, mid, ops)[0] > 3.0:
+            hi = mid
+        else:
+            lo = mid
+    root = 0.5 * (lo + hi)
+    slope = gw.particle_number_and_slope(H, S, Shf, Sig, root, ops)[1]
+    for start in (0.0, root + 0.3, -19.0, 25.0):
+        _, mu = gw.dyson(H, S, Shf, Sig, start, ops, n_elec=3.0, search_mu=True)
+        n = gw.particle_number_and_slope(H, S, Shf, Sig, mu, ops)[0]
+        assert abs(n - 3.0) <= 1e-11
+        assert abs(mu - root) <= 2e-11 / slope + 1e-13
+
+
 def test_energy_without_interaction_is_band_energy(small):
     H, S, beta, mu = small["H"], small["S"], small["beta"], small["mu"]
     Nk, n = H.shape[0], small["n"]
@@ -206,3 +251,14 @@ def test_planted_mistakes_fail_the_pins(small):
     # (4) orbital indices of V transposed in Sigma -> the trace identity fails
     Sig_bad2 = gw.self_energy(small["G"], good, lambda a, b: V[a, b].transpose(0, 2, 1), NK)
     assert _trace_identity_residual(small["G"], good, Sig_bad2) > 1e-3
+    # (5) dG/dmu taken as -G G (the overlap dropped) -> the slope is no longer the derivative
+    H, S = small["H"], small["S"]
+    Shf, Sig = _interacting_sigma(small)
+    Sw = gw.to_matsubara(Sig, ops["TF"])
+    wgt = -(grid.value_at_beta_minus(ops["TF"].shape[1]) @ ops["TFbar"])
+    Gw = gw.dyson_matsubara(H, S, Shf, Sw, 0.1, ops["nu_f"])
+    slip = gw.particle_number(-np.einsum("m,kmij,kmjl->kil", wgt, Gw, Gw), S)
+    h = 1e-5
+    fd = (gw.particle_number_and_slope(H, S, Shf, Sig, 0.1 + h, ops)[0]
+          - gw.particle_number_and_slope(H, S, Shf, Sig, 0.1 - h, ops)[0]) / (2 * h)
+    assert abs(slip - fd) > 1e-3 * abs(fd)
