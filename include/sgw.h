@@ -238,9 +238,14 @@ SGW_API sgw_status sgw_screened_interaction_noalloc(sgw_ctx* ctx, const void* P0
 SGW_API sgw_status sgw_hartree_fock(sgw_ctx* ctx, const void* G_tau, void* Sigma_hf, sgw_stream stream);
 /* a8 + a9 + a10: Sigma~(tau) -> Sigma~(i w); G(i w) = [(i w + mu) S - H0 -
  * Sigma_HF - Sigma~(i w)]^{-1} per block (Eq. (dyson)); G(tau).  With
- * search_mu != 0, mu is found by bisection on [-20, 20] so that
- * (s/N_k) sum_k Tr[gamma^k S^k] = n_elec (stop at |N - n_elec| <= 1e-11 or
- * after 64 halvings); synchronous in that case.  *mu_inout is host. */
+ * search_mu != 0, mu solves N(mu) = (s/N_k) sum_k Tr[gamma^k S^k] = n_elec
+ * by Newton's method kept inside the bracket [-20, 20] (N'(mu) from
+ * dG/dmu = -G S G; a Newton point outside the current bracket, or one that
+ * follows a trial which did not halve |N - n_elec|, is replaced by the
+ * bracket's midpoint), starting from *mu_inout (the midpoint when outside
+ * the bracket); it stops at |N - n_elec| <= 1e-11 or after 64 trials, and is
+ * synchronous in that case.  *mu_inout is host: the start (or the fixed mu
+ * without the search) in, the result out. */
 SGW_API sgw_status sgw_dyson(sgw_ctx* ctx, const void* Sigma_tau, const void* Sigma_hf, double* mu_inout,
                              int search_mu, void* G_tau, sgw_stream stream);
 /* a12: total energy (Galitskii-Migdal form; the paper defines none) into
@@ -251,7 +256,9 @@ SGW_API sgw_status sgw_energy(sgw_ctx* ctx, const void* G_tau, const void* Sigma
  * Sigma <- (1-damping) Sigma_old + damping Sigma_new -> Dyson with mu search,
  * until max |Sigma_new - Sigma_old| < tol or max_iter passes.  G_tau
  * (in/out), Sigma_tau, Sigma_hf (in/out; zero on the first pass) are packed;
- * *mu is host in/out.  Synchronous; fills *stats (host, may be NULL). */
+ * *mu is host in/out: each pass's mu search (as in sgw_dyson) starts from the
+ * mu of the pass before, the first from *mu.  Synchronous; fills *stats
+ * (host, may be NULL). */
 SGW_API sgw_status sgw_iterate(sgw_ctx* ctx, int max_iter, double damping, double tol, void* G_tau,
                                void* Sigma_tau, void* Sigma_hf, double* mu, sgw_iter_stats* stats,
                                sgw_stream stream);

@@ -274,6 +274,7 @@ extern "C" SGW_API sgw_status sgw_create(const sgw_params* p, sgw_ctx** out) {
     return SGW_ERR_OOM;
   }
   cudaMemset(c->d_status, 0, sizeof(int));
+  cudaMemset(c->d_scalar, 0, 64 * sizeof(double));
   *out = c;
   return SGW_OK;
 }
@@ -1266,12 +1267,13 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
 // ---------------------------------------------------------------------------
 // a8-a10: Dyson with the chemical-potential search
 // ---------------------------------------------------------------------------
-// Dyson for the whole wedge at one chemical potential, or with the bisection search of mu.
-// The search runs entirely on the device (no host round trip per trial): a fixed number of
-// trial launches whose later members do nothing once the search has stopped.  The final mu
-// is left in d_scalar[2].
+// Dyson for the whole wedge at one chemical potential, or with the search of mu (bracketed
+// Newton from the start point mu, or *mu_start_dev when given).  The search runs entirely on
+// the device (no host round trip per trial): a fixed number of trial launches whose later
+// members do nothing once the search has stopped.  The final mu is left in d_scalar[2].
 static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const double2* Sigma_hf, double mu,
-                               int search_mu, double2* G_tau, cudaStream_t st) {
+                               int search_mu, double2* G_tau, cudaStream_t st,
+                               const double* mu_start_dev = nullptr) {
   CKS(ensure_tables(c));
   const long long ge = c->g_elems;
   const int nwf = c->nwf;
@@ -1292,18 +1294,18 @@ static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const doubl
   CK(cudaMemcpyAsync(F, c->d_H0, ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   run(c, "axpby", 0.0, 1, st, [&] { axpby(F, Sigma_hf, ge, 1.0, 1.0, st); });
   double* s = c->d_scalar;
-  double2* d_sum = reinterpret_cast<double2*>(c->d_scalar + 8);
   const double* mu_dev = nullptr;
   if (search_mu) {
-    run(c, "mu_search", 0.0, 1, st, [&] { mu_step(0, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
+    run(c, "mu_search", 0.0, 1, st, [&] { mu_start(s, mu, mu_start_dev, -20.0, 20.0, st); });
+    // a trial inverts every block (n^3) and forms G S (n^3) for the slope; the flops of the
+    // trials that ran are added from the device's trial count when the profile is read
+    c->dy_trial_flops = 2.0 * fli;
     for (int it = 0; it < 64; ++it) {
-      run(c, "mu_search", 0.0, 1, st, [&] { mu_step(1, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
-      run(c, "dyson_invert", fli, 1, st, [&] {
+      run(c, "dyson_invert", 0.0, 1, st, [&] {
         invert_blocks_split(INV_DYSON_TRACE, c->d_dy_items, c->n_dy_small, c->dy_small_n, c->n_dy_items, maxn, Sw, c->d_S, F,
                             c->d_nu_f, 0.0, s + 2, s + 3, nullptr, tpart, scr, c->d_status, st);
       });
-      run(c, "reduce", 0.0, 1, st, [&] { sum_partials(tpart, c->n_dy_items, d_sum, st); });
-      run(c, "mu_search", 0.0, 1, st, [&] { mu_step(2, s, d_sum, c->p.n_elec, 1e-11, -20.0, 20.0, st); });
+      run(c, "mu_search", 0.0, 1, st, [&] { mu_update(s, tpart, c->n_dy_items, c->p.n_elec, 1e-11, st); });
     }
     mu_dev = s + 2;
   }
@@ -1427,7 +1429,9 @@ static sgw_status iteration_body(sgw_ctx* c, double damping, double2* G, double2
   run(c, "reduce", 0.0, 1, st, [&] { max_abs_diff(c->d_it_H, Hf, ge, c->d_maxbits + 1, st); });
   CK(cudaMemcpyAsync(Sig, c->d_it_S, (size_t)nt * ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(Hf, c->d_it_H, (size_t)ge * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  CKS(dyson_device(c, Sig, Hf, 0.0, 1, G, st));
+  // the search starts at the mu the host put in h_pinned[12] before this pass (read when the pass runs)
+  CK(cudaMemcpyAsync(c->d_scalar + 6, c->h_pinned + 12, sizeof(double), cudaMemcpyHostToDevice, st));
+  CKS(dyson_device(c, Sig, Hf, 0.0, 1, G, st, c->d_scalar + 6));
   CK(cudaMemcpyAsync(c->h_pinned, c->d_scalar, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(c->h_pinned + 8, c->d_maxbits, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   return SGW_OK;
@@ -1487,6 +1491,7 @@ extern "C" SGW_API sgw_status sgw_iterate(sgw_ctx* c, int max_iter, double dampi
   double dmax = 0.0;
   int it = 0;
   for (it = 0; it < max_iter; ++it) {
+    c->h_pinned[12] = *mu;  // start of this pass's mu search (the stream is idle here)
     if (graph) {
       CK(cudaGraphLaunch(c->it_exec, st));
     } else {
@@ -1589,8 +1594,16 @@ extern "C" SGW_API sgw_status sgw_unfold(sgw_ctx* c, int which, int nt, const vo
 // ---------------------------------------------------------------------------
 // instrumentation
 // ---------------------------------------------------------------------------
+// running count of evaluated mu-search trials (d_scalar[16]); synchronises the device
+static double trials_done(sgw_ctx* c) {
+  double v = 0.0;
+  if (c->d_scalar && cudaDeviceSynchronize() == cudaSuccess && cudaMemcpy(&v, c->d_scalar + 16, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) v = 0.0;
+  return v;
+}
+
 extern "C" SGW_API sgw_status sgw_profile_enable(sgw_ctx* c, int on) {
   if (!c) return SGW_ERR_ARG;
+  if (on && !c->prof_on) c->prof_trials_seen = trials_done(c);
   c->prof_on = on != 0;
   return SGW_OK;
 }
@@ -1607,6 +1620,12 @@ extern "C" SGW_API sgw_status sgw_profile_read(sgw_ctx* c, int max_entries, char
     cudaEventDestroy(e.b);
   }
   c->prof_pending.clear();
+  if (c->dy_trial_flops > 0.0) {
+    const double t = trials_done(c);
+    for (size_t i = 0; i < c->prof_names.size(); ++i)
+      if (c->prof_names[i] == "dyson_invert") c->prof_flops[i] += (t - c->prof_trials_seen) * c->dy_trial_flops;
+    c->prof_trials_seen = t;
+  }
   const int n = (int)c->prof_names.size();
   *n_out = n;
   for (int i = 0; i < n && i < max_entries; ++i) {

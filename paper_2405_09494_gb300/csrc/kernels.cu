@@ -506,7 +506,8 @@ void series_map(const double2* T, int nm, int nt, const double2* in, long long i
 // global scratch buffer (the algorithm is the same on either).
 //   INV_W          : A = I - P0(i Omega)_B          -> out = A^{-1} - I = [I - P0]^{-1} P0
 //   INV_DYSON_STORE: A = (i w + mu) S - F - Sigma(i w) -> out = A^{-1} = G(i w)
-//   INV_DYSON_TRACE: as above, trace_partial[item] = weight * Re Tr[A^{-1} S]
+//   INV_DYSON_TRACE: as above, trace_partial[item] = (Re weight Tr[G S], -Re weight Tr[G S G S])
+//                    with G = A^{-1}: the item's share of N(mu) and of dN/dmu (dG/dmu = -G S G)
 // ---------------------------------------------------------------------------
 constexpr int kInvSmemMaxN = 90;
 
@@ -619,21 +620,38 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
     } else if (mode == INV_DYSON_STORE) {
       for (int e = tid; e < nn; e += blockDim.x) out[it.out_off + e] = A[e];
     } else {
-      double2 s = make_double2(0.0, 0.0);
+      // Tr[G S] and Tr[(G S)^2]; thread e forms X_ij = (G S)_ij and X_ji without storing X
+      const double2* Sb = S + it.s_off;
+      double2 s = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
       for (int e = tid; e < nn; e += blockDim.x) {
         const int i = e / n, j = e - i * n;
-        s = cfma(A[e], S[it.s_off + j * n + i], s);  // G_ij S_ji
+        double2 xij = make_double2(0.0, 0.0), xji = make_double2(0.0, 0.0);
+        for (int l = 0; l < n; ++l) {
+          xij = cfma(A[i * n + l], Sb[l * n + j], xij);
+          xji = cfma(A[j * n + l], Sb[l * n + i], xji);
+        }
+        if (i == j) s = cadd(s, xij);
+        s2 = cfma(xij, xji, s2);
       }
+      __shared__ double s_red2[256], s_red2i[256];
       s_red[tid] = s.x;
       s_redi[tid] = s.y;
+      s_red2[tid] = s2.x;
+      s_red2i[tid] = s2.y;
       __syncthreads();
       for (int off = 128; off > 0; off >>= 1) {
-        if (tid < off) { s_red[tid] += s_red[tid + off]; s_redi[tid] += s_redi[tid + off]; }
+        if (tid < off) {
+          s_red[tid] += s_red[tid + off];
+          s_redi[tid] += s_redi[tid + off];
+          s_red2[tid] += s_red2[tid + off];
+          s_red2i[tid] += s_red2i[tid + off];
+        }
         __syncthreads();
       }
       if (tid == 0) {
         const double2 t = cmul(it.weight, make_double2(s_red[0], s_redi[0]));
-        tpart[it.slot] = make_double2(t.x, 0.0);
+        const double2 d = cmul(it.weight, make_double2(s_red2[0], s_red2i[0]));
+        tpart[it.slot] = make_double2(t.x, -d.x);  // (N part, dN/dmu part): dG/dmu = -G S G
       }
     }
     __syncthreads();
@@ -644,6 +662,7 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
 // one warp-wide argmax, one row swap and one scaled-row broadcast; every lane then updates its
 // own row with independent multiply-adds (no serial chain over rows).
 constexpr int kWarpInvN = 32;
+constexpr int kWarpInvSmemMax = 8 * kWarpInvN * (kWarpInvN + 1) * (int)sizeof(double2);  // 135168 B
 __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __restrict__ items, int nitems,
                                                      const double2* __restrict__ Asrc, const double2* __restrict__ S,
                                                      const double2* __restrict__ F, const double* __restrict__ nu,
@@ -651,16 +670,19 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
                                                      const double* __restrict__ done_dev, double2* __restrict__ out,
                                                      double2* __restrict__ tpart, int* __restrict__ status,
                                                      int slot_n) {
-  // dynamic shared memory: 8 warp slots of slot_n rows x (slot_n + 1) complex (padded rows)
+  // dynamic shared memory: one slot per warp of slot_n rows x (slot_n + 1) complex (padded rows),
+  // two in the trace mode (the inverse, then X = G S)
   extern __shared__ double2 smdyn[];
   if (done_dev != nullptr && *done_dev != 0.0) return;
   const double mu = mu_dev != nullptr ? *mu_dev : mu_host;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int itx = blockIdx.x * 8 + warp;
+  const int wpc = blockDim.x >> 5;
+  const int itx = blockIdx.x * wpc + warp;
   if (itx >= nitems) return;
   const InvItem it = items[itx];
   const int n = it.n, ld = slot_n + 1;
-  double2* A = smdyn + (long long)warp * slot_n * ld;
+  const int nbuf = mode == INV_DYSON_TRACE ? 2 : 1;
+  double2* A = smdyn + (long long)warp * nbuf * slot_n * ld;
   for (int e = lane; e < n * n; e += 32) {
     const int i = e / n, j = e - i * n;
     double2 a;
@@ -742,18 +764,32 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
       out[it.out_off + e] = A[i * ld + j];
     }
   } else {
-    double2 s = make_double2(0.0, 0.0);
-    for (int e = lane; e < n * n; e += 32) {
-      const int i = e / n, j = e - i * n;
-      s = cfma(A[i * ld + j], S[it.s_off + j * n + i], s);
+    // lane i: row i of X = G S into the second slot, then X_ii and sum_j X_ij X_ji
+    double2* X = A + slot_n * ld;
+    const double2* Sb = S + it.s_off;
+    if (lane < n) {
+      for (int j = 0; j < n; ++j) {
+        double2 x = make_double2(0.0, 0.0);
+        for (int l = 0; l < n; ++l) x = cfma(row[l], Sb[l * n + j], x);
+        X[lane * ld + j] = x;
+      }
+    }
+    __syncwarp();
+    double2 s = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
+    if (lane < n) {
+      s = X[lane * ld + lane];
+      for (int j = 0; j < n; ++j) s2 = cfma(X[lane * ld + j], X[j * ld + lane], s2);
     }
     for (int off = 16; off > 0; off >>= 1) {
       s.x += __shfl_down_sync(0xffffffffu, s.x, off);
       s.y += __shfl_down_sync(0xffffffffu, s.y, off);
+      s2.x += __shfl_down_sync(0xffffffffu, s2.x, off);
+      s2.y += __shfl_down_sync(0xffffffffu, s2.y, off);
     }
     if (lane == 0) {
       const double2 t = cmul(it.weight, s);
-      tpart[it.slot] = make_double2(t.x, 0.0);
+      const double2 d = cmul(it.weight, s2);
+      tpart[it.slot] = make_double2(t.x, -d.x);  // (N part, dN/dmu part)
     }
   }
 }
@@ -765,14 +801,14 @@ void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_sma
   if (nsmall > 0) {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(8 * kWarpInvN * (kWarpInvN + 1) * sizeof(double2)));
+      cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpInvSmemMax);
       attr = true;
     }
     const int sn = max_small_n < 1 ? 1 : max_small_n;
-    const size_t sm = (size_t)8 * sn * (sn + 1) * sizeof(double2);
-    k_invert_warp<<<(nsmall + 7) / 8, 256, sm, st>>>(mode, items, nsmall, A, S, F, nu, mu, mu_dev, done_dev, out,
-                                                     trace_partial, status, sn);
+    const size_t per_warp = (size_t)(mode == INV_DYSON_TRACE ? 2 : 1) * sn * (sn + 1) * sizeof(double2);
+    const int wpc = 8 * per_warp <= (size_t)kWarpInvSmemMax ? 8 : 4;  // 4 x 2 x 32 x 33 x 16 B fits
+    k_invert_warp<<<(nsmall + wpc - 1) / wpc, 32 * wpc, wpc * per_warp, st>>>(
+        mode, items, nsmall, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial, status, sn);
   }
   if (nitems > nsmall)
     invert_blocks(mode, items + nsmall, nitems - nsmall, max_n, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial,
@@ -1121,27 +1157,57 @@ void g0_closed_form(const double2* C, const double* eps, const long long* row_bo
                                                               beta, mu, G);
 }
 
-// One step of the chemical-potential bisection, decided on the device.  s[0] lo, s[1] hi,
-// s[2] mu (the trial), s[3] done, s[4] N of the last trial.  mode 0: start the search on
-// [lo, hi]; mode 1: new trial mu = (lo + hi) / 2 unless done; mode 2: read N(mu) and either
-// stop (|N - target| <= tol) or halve the bracket (N > target: hi = mu, else lo = mu).
-__global__ void k_mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi) {
+// Chemical-potential search on the device (bracketed Newton).  State s[0] lo, s[1] hi, s[2] mu
+// (the next trial, then the result), s[3] done, s[4] N of the last trial, s[5] |N - target| of
+// the previous trial, s[16] running count of evaluated trials.  k_mu_start: the first trial is the start point when it lies inside
+// (lo, hi), else the midpoint.  k_mu_update: sums the trial's partials (N, dN/dmu) in a fixed
+// order and either stops (|N - target| <= tol) or shrinks the bracket to the side holding the
+// root and picks the next trial: the Newton point mu - (N - target) / N' when N' > 0, the point
+// lies strictly inside the bracket and |N - target| fell to at most half its previous value,
+// else the midpoint of the bracket.
+__global__ void k_mu_start(double* s, double start_host, const double* start_dev, double lo, double hi) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (mode == 0) {
-    s[0] = lo; s[1] = hi; s[2] = 0.5 * (lo + hi); s[3] = 0.0; s[4] = 0.0;
-  } else if (mode == 1) {
-    if (s[3] == 0.0) s[2] = 0.5 * (s[0] + s[1]);
-  } else if (s[3] == 0.0) {
-    const double n = nsum->x;
-    s[4] = n;
-    if (fabs(n - target) <= tol) s[3] = 1.0;
-    else if (n > target) s[1] = s[2];
-    else s[0] = s[2];
-  }
+  const double m = start_dev != nullptr ? *start_dev : start_host;
+  s[0] = lo;
+  s[1] = hi;
+  s[2] = (m > lo && m < hi) ? m : 0.5 * (lo + hi);
+  s[3] = 0.0;
+  s[4] = 0.0;
+  s[5] = INFINITY;
 }
-void mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi,
-             cudaStream_t st) {
-  k_mu_step<<<1, 32, 0, st>>>(mode, s, nsum, target, tol, lo, hi);
+__global__ void __launch_bounds__(256) k_mu_update(double* s, const double2* __restrict__ partial, int n,
+                                                   double target, double tol) {
+  if (s[3] != 0.0) return;
+  __shared__ double2 red[256];
+  double2 a = make_double2(0, 0);
+  for (int i = threadIdx.x; i < n; i += 256) a = cadd(a, partial[i]);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + off]);
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double nn = red[0].x, dn = red[0].y, mu = s[2];
+  const double r = nn - target;
+  s[4] = nn;
+  s[16] += 1.0;  // trials evaluated since the context was made (for flop accounting)
+  if (fabs(r) <= tol) {
+    s[3] = 1.0;
+    return;
+  }
+  if (r > 0) s[1] = mu;
+  else s[0] = mu;
+  const double lo = s[0], hi = s[1];
+  const double newton = dn > 0 ? mu - r / dn : NAN;
+  s[2] = (newton > lo && newton < hi && fabs(r) <= 0.5 * s[5]) ? newton : 0.5 * (lo + hi);
+  s[5] = fabs(r);
+}
+void mu_start(double* s, double start_host, const double* start_dev, double lo, double hi, cudaStream_t st) {
+  k_mu_start<<<1, 32, 0, st>>>(s, start_host, start_dev, lo, hi);
+}
+void mu_update(double* s, const double2* partial, int n, double target, double tol, cudaStream_t st) {
+  k_mu_update<<<1, 256, 0, st>>>(s, partial, n, target, tol);
 }
 
 // mu by bisection on (sum_i w_i f(eps_i - mu)) = target, one CTA, fixed 200 halvings.

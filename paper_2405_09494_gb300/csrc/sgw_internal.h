@@ -105,7 +105,7 @@ struct InvItem {
   int n;
   int m;             // frequency index (Dyson)
   int slot;          // trace partial slot (Dyson number mode)
-  double2 weight;    // trace weight (Dyson number mode): partial = Re(weight * Tr[A^{-1} S])
+  double2 weight;    // trace weight (Dyson number mode): partial = (Re weight Tr[G S], -Re weight Tr[G S G S])
 };
 enum InvMode { INV_W = 0, INV_DYSON_STORE = 1, INV_DYSON_TRACE = 2 };
 void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
@@ -116,8 +116,8 @@ void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_sma
                          const double2* A, const double2* S, const double2* F, const double* nu, double mu,
                          const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
                          double2* scratch, int* status, cudaStream_t st);
-void mu_step(int mode, double* s, const double2* nsum, double target, double tol, double lo, double hi,
-             cudaStream_t st);
+void mu_start(double* s, double start_host, const double* start_dev, double lo, double hi, cudaStream_t st);
+void mu_update(double* s, const double2* partial, int n, double target, double tol, cudaStream_t st);
 
 // Batched generalised Hermitian eigensolver H C = S C eps (S may be null: identity).
 struct EigItem {
@@ -253,6 +253,8 @@ struct sgw_ctx {
   size_t ws_bytes = 0;
   int* d_status = nullptr;
   double* d_scalar = nullptr;  // small host-visible results
+  double dy_trial_flops = 0.0; // algorithmic flops of one mu-search trial (set by Dyson)
+  double prof_trials_seen = 0.0; // trial count (d_scalar[16]) when profiling was last switched on / read
   unsigned long long* d_maxbits = nullptr;
 
   // launch accounting and optional per-kernel CUDA-event timing
