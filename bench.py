@@ -38,6 +38,9 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 
 # the chosen form spends three TF32 products per FP32-accurate product
 TF32_X3_PEAK_TFLOPS = 1907.2 * 1.1 / 2.25 / 3
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one launch of a kernel class on a workload, from one ncu capture
+# (profiles/k_bd_mult_fp64_c2.md); reported as the roofline's traffic while the kernel is unchanged.
+DRAM_TRAFFIC_BYTES = {("c2", "sigma_pvg"): 4654034944 + 2777765888}
 
 
 def _args():
@@ -276,7 +279,7 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     return out
 
 
-def _roofline(prof):
+def _roofline(prof, workload=None):
     """Roofline of the kernel class with the most device time, against the peak of the pipe it runs on."""
     compute = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(compute, key=lambda k: compute[k][0])
@@ -293,7 +296,7 @@ def _roofline(prof):
         bound, peak, note = "alu", FP64_PEAK_TFLOPS, (
             "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived; a DFMA probe measured 1.20)")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "peak_note": note}
+            "frac": achieved / peak, "traffic": DRAM_TRAFFIC_BYTES.get((workload, dom)), "peak_note": note}
 
 
 def _kernels(prof, steps):
@@ -361,7 +364,7 @@ def run_ours(args, rank, world, local):
     def summary(f):
         r = res[f]
         gf = sum(v[1] for v in r["prof"].values()) / args.steps
-        return gf, _roofline(r["prof"])
+        return gf, _roofline(r["prof"], cfg.name)
 
     head = forms[0]
     gf_h, roof_h = summary(head)
