@@ -296,6 +296,10 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
   dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
+  for (auto& a : c->inv_aux)
+    if (a) cudaStreamDestroy(a);
+  for (auto& e : c->inv_ev)
+    if (e) cudaEventDestroy(e);
   dfree(c->d_it_P0); dfree(c->d_it_P); dfree(c->d_it_S); dfree(c->d_it_H);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->it_exec) cudaGraphExecDestroy(c->it_exec);
@@ -857,24 +861,48 @@ static sgw_status ensure_tables(sgw_ctx* c) {
   for (size_t b = 0; b < nb; ++b) bn[b] = c->aob_n[b];
   const int wG = c->rep[0];
   for (int w = 0; w < c->nwedge; ++w) tab[3 * nb + w] = ((long long)wG * c->Nk + c->wedge_k[w]) * vs;
-  // warp-sized blocks first (one warp each), larger blocks after (one CTA each); slots keep the
+  // three groups (warp-sized blocks, blocks above 90 in global scratch, the rest in shared
+  // memory), each ordered largest first so the longest eliminations start first; slots keep the
   // original order so the trace partials are summed in a fixed order
-  auto split = [](std::vector<InvItem>& v, int& max_small) {
+  auto group = [](const InvItem& x) { return x.n <= 32 ? 0 : x.n > 90 ? 1 : 2; };
+  auto split = [&](std::vector<InvItem>& v, InvPlan& pl) {
     for (size_t i = 0; i < v.size(); ++i) v[i].slot = (int)i;
-    std::stable_partition(v.begin(), v.end(), [](const InvItem& x) { return x.n <= 32; });
-    int ns = 0;
-    max_small = 1;
-    for (auto& x : v)
-      if (x.n <= 32) { ++ns; max_small = std::max(max_small, x.n); }
-    return ns;
+    std::stable_sort(v.begin(), v.end(), [&](const InvItem& a, const InvItem& b) {
+      const int ga = group(a), gb = group(b);
+      return ga != gb ? ga < gb : a.n > b.n;
+    });
+    pl = InvPlan();
+    pl.nitems = (int)v.size();
+    for (auto& x : v) {
+      const int g = group(x);
+      if (g == 0) { ++pl.nsmall; pl.small_n = std::max(pl.small_n, x.n); }
+      else if (g == 1) ++pl.nscr;
+      else pl.mid_n = std::max(pl.mid_n, x.n);
+      pl.max_n = std::max(pl.max_n, x.n);
+    }
   };
-  c->n_w_small = split(w, c->w_small_n);
-  c->n_dy_small = split(d, c->dy_small_n);
+  split(w, c->w_plan);
+  split(d, c->dy_plan);
+  if (c->w_plan.max_n > 1024 || c->dy_plan.max_n > 1024)
+    return c->fail(SGW_ERR_ARG, "irrep blocks above 1024 are not supported by the inversion kernels");
   CKS(upload(c, c->d_w_items, w));
   CKS(upload(c, c->d_dy_items, d));
   CKS(upload(c, c->d_hf_tab, tab));
   c->n_w_items = (int)w.size();
   c->n_dy_items = (int)d.size();
+  if (!c->inv_aux[0]) {
+    for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&c->inv_aux[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&c->inv_ev[i], cudaEventDisableTiming));
+  }
+  for (InvPlan* pl : {&c->w_plan, &c->dy_plan}) {
+    pl->aux[0] = c->inv_aux[0];
+    pl->aux[1] = c->inv_aux[1];
+    pl->fork = c->inv_ev[0];
+    pl->join[0] = c->inv_ev[1];
+    pl->join[1] = c->inv_ev[2];
+  }
+  c->w_plan.items = c->d_w_items;
+  c->dy_plan.items = c->d_dy_items;
   c->tables = true;
   return SGW_OK;
 }
@@ -902,8 +930,8 @@ extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P
     series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, z(1.0), 0, st);
   });
   run(c, "w_solve", flw, 1, st, [&] {
-    invert_blocks_split(INV_W, c->d_w_items, c->n_w_small, c->w_small_n, c->n_w_items, maxn, P0w, nullptr, nullptr, nullptr, 0.0,
-                        nullptr, nullptr, Pw, nullptr, scr, c->d_status, st);
+    invert_plan(INV_W, c->w_plan, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, scr, c->d_status,
+                st);
   });
   run(c, "ft", flt, 1, st, [&] {
     series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, z(1.0), 0, st);
@@ -1302,16 +1330,16 @@ static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const doubl
     c->dy_trial_flops = 2.0 * fli;
     for (int it = 0; it < 64; ++it) {
       run(c, "dyson_invert", 0.0, 1, st, [&] {
-        invert_blocks_split(INV_DYSON_TRACE, c->d_dy_items, c->n_dy_small, c->dy_small_n, c->n_dy_items, maxn, Sw, c->d_S, F,
-                            c->d_nu_f, 0.0, s + 2, s + 3, nullptr, tpart, scr, c->d_status, st);
+        invert_plan(INV_DYSON_TRACE, c->dy_plan, Sw, c->d_S, F, c->d_nu_f, 0.0, s + 2, s + 3, nullptr, tpart, scr,
+                    c->d_status, st);
       });
       run(c, "mu_search", 0.0, 1, st, [&] { mu_update(s, tpart, c->n_dy_items, c->p.n_elec, 1e-11, st); });
     }
     mu_dev = s + 2;
   }
   run(c, "dyson_invert", fli, 1, st, [&] {
-    invert_blocks_split(INV_DYSON_STORE, c->d_dy_items, c->n_dy_small, c->dy_small_n, c->n_dy_items, maxn, Sw, c->d_S, F, c->d_nu_f,
-                        mu, mu_dev, nullptr, Gw, nullptr, scr, c->d_status, st);
+    invert_plan(INV_DYSON_STORE, c->dy_plan, Sw, c->d_S, F, c->d_nu_f, mu, mu_dev, nullptr, Gw, nullptr, scr,
+                c->d_status, st);
   });
   run(c, "ft", 8.0 * nwf * (double)c->nt * ge, 1, st, [&] {
     series_map(c->d_TFbar, c->nt, nwf, Gw, ge, G_tau, ge, ge, z(1.0), 0, st);

@@ -501,60 +501,75 @@ void series_map(const double2* T, int nm, int nt, const double2* in, long long i
 }
 
 // ---------------------------------------------------------------------------
-// Batched Gauss-Jordan inversion with partial pivoting, one CTA per block.
-// Small blocks live in shared memory; larger ones in a per-CTA slot of the
-// global scratch buffer (the algorithm is the same on either).
+// Batched Gauss-Jordan inversion with partial pivoting.
 //   INV_W          : A = I - P0(i Omega)_B          -> out = A^{-1} - I = [I - P0]^{-1} P0
 //   INV_DYSON_STORE: A = (i w + mu) S - F - Sigma(i w) -> out = A^{-1} = G(i w)
 //   INV_DYSON_TRACE: as above, trace_partial[item] = (Re weight Tr[G S], -Re weight Tr[G S G S])
 //                    with G = A^{-1}: the item's share of N(mu) and of dN/dmu (dG/dmu = -G S G)
+// Blocks of up to 32 take one warp each (k_invert_warp); larger ones one CTA of 8 warps each
+// (k_invert_cta), the matrix in shared memory up to n = 90 (rows padded to an odd stride, so a
+// column read by 32 threads takes the minimum number of wavefronts) and in a per-CTA slot of a
+// global scratch buffer (L2-resident) above.
 // ---------------------------------------------------------------------------
 constexpr int kInvSmemMaxN = 90;
+constexpr int kInvMaxN = 1024;  // bound of the per-CTA pivot and column arrays
+constexpr int kInvScratchSlots = 304;
 
-__global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restrict__ items, int nitems, int max_n,
-                                                const double2* __restrict__ Asrc, const double2* __restrict__ S,
-                                                const double2* __restrict__ F, const double* __restrict__ nu,
-                                                double mu_host, const double* __restrict__ mu_dev,
-                                                const double* __restrict__ done_dev, double2* __restrict__ out,
-                                                double2* __restrict__ tpart, double2* __restrict__ scratch,
-                                                int* __restrict__ status, int use_smem) {
+// CTA per block.  Step k of the elimination: (1) every thread copies column k, warp 0 finds the
+// pivot row p (largest |a_ik|, i >= k); (2) rows k and p are exchanged and the new pivot row is
+// scaled by 1/a_pk, its diagonal set to 1/a_pk; (3) each warp takes rows i != k, its lanes the
+// columns j: a_ij <- [j != k] a_ij - c_i a_kj with c_i row i's column-k entry after the exchange.
+// Rows are spread over warps and columns over lanes, so no thread divides an index.  The column
+// exchanges that undo the row pivoting are applied row by row at the end (each thread walks its
+// own rows through the swap sequence in reverse).
+__global__ void __launch_bounds__(256) k_invert_cta(int mode, const InvItem* __restrict__ items, int nitems,
+                                                    int slot_elems, const double2* __restrict__ Asrc,
+                                                    const double2* __restrict__ S, const double2* __restrict__ F,
+                                                    const double* __restrict__ nu, double mu_host,
+                                                    const double* __restrict__ mu_dev,
+                                                    const double* __restrict__ done_dev, double2* __restrict__ out,
+                                                    double2* __restrict__ tpart, double2* __restrict__ scratch,
+                                                    int* __restrict__ status, int use_smem) {
   if (done_dev != nullptr && *done_dev != 0.0) return;  // a finished search skips its remaining trials
   const double mu = mu_dev != nullptr ? *mu_dev : mu_host;
   extern __shared__ double2 smem[];
-  __shared__ double2 col[640];
-  __shared__ int perm[640];
+  __shared__ double2 col[kInvMaxN];
+  __shared__ int perm[kInvMaxN];
   __shared__ int s_piv;
-  __shared__ double s_red[256];
-  __shared__ double s_redi[256];
-  const int tid = threadIdx.x;
-  double2* A = use_smem ? smem : scratch + (long long)blockIdx.x * max_n * max_n;
+  __shared__ double s_red[4][8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NW = 8;
+  double2* A = use_smem ? smem : scratch + (long long)blockIdx.x * slot_elems;
   for (int itx = blockIdx.x; itx < nitems; itx += gridDim.x) {
     const InvItem it = items[itx];
     const int n = it.n;
-    const int nn = n * n;
+    const int ld = use_smem ? (n | 1) : n;
     // assemble
-    for (int e = tid; e < nn; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      double2 a;
-      if (mode == INV_W) {
-        const double2 p = Asrc[it.a_off + e];
-        a = make_double2((i == j ? 1.0 : 0.0) - p.x, -p.y);
-      } else {
-        const double2 s = S[it.s_off + e], f = F[it.f_off + e], sg = Asrc[it.a_off + e];
-        const double w = nu[it.m];
-        // (i w + mu) s - f - sigma
-        a.x = mu * s.x - w * s.y - f.x - sg.x;
-        a.y = mu * s.y + w * s.x - f.y - sg.y;
+    for (int i = warp; i < n; i += NW) {
+      for (int j = lane; j < n; j += 32) {
+        const long long e = (long long)i * n + j;
+        double2 a;
+        if (mode == INV_W) {
+          const double2 pv = Asrc[it.a_off + e];
+          a = make_double2((i == j ? 1.0 : 0.0) - pv.x, -pv.y);
+        } else {
+          const double2 sv = S[it.s_off + e], fv = F[it.f_off + e], sg = Asrc[it.a_off + e];
+          const double w = nu[it.m];
+          a.x = mu * sv.x - w * sv.y - fv.x - sg.x;  // (i w + mu) s - f - sigma
+          a.y = mu * sv.y + w * sv.x - fv.y - sg.y;
+        }
+        A[i * ld + j] = a;
       }
-      A[e] = a;
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-      if (tid < 32) {
+      // (1) column k and the pivot
+      for (int i = tid; i < n; i += blockDim.x) col[i] = A[i * ld + k];
+      if (warp == 0) {
         double best = -1.0;
         int bi = k;
-        for (int i = k + tid; i < n; i += 32) {
-          const double v = cabs2(A[i * n + k]);
+        for (int i = k + lane; i < n; i += 32) {
+          const double v = cabs2(A[i * ld + k]);
           if (v > best) { best = v; bi = i; }
         }
         for (int off = 16; off > 0; off >>= 1) {
@@ -562,96 +577,95 @@ __global__ void __launch_bounds__(256) k_invert(int mode, const InvItem* __restr
           const int oi = __shfl_down_sync(0xffffffffu, bi, off);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (tid == 0) { s_piv = bi; perm[k] = bi; }
+        if (lane == 0) { s_piv = bi; perm[k] = bi; }
       }
       __syncthreads();
       const int p = s_piv;
-      if (p != k) {
-        for (int j = tid; j < n; j += blockDim.x) {
-          const double2 t = A[k * n + j];
-          A[k * n + j] = A[p * n + j];
-          A[p * n + j] = t;
-        }
-        __syncthreads();
-      }
-      double2 piv = A[k * n + k];
+      double2 piv = col[p];
       const double pm = cabs2(piv);
       if (!(pm > 1e-300)) {
         if (tid == 0) atomicExch(status, (int)DEV_SINGULAR);
         piv = make_double2(1.0, 0.0);
       }
-      const double2 inv = make_double2(piv.x / pm, -piv.y / pm);
-      for (int i = tid; i < n; i += blockDim.x) col[i] = A[i * n + k];
+      const double den = pm > 1e-300 ? pm : 1.0;
+      const double2 inv = make_double2(piv.x / den, -piv.y / den);
+      // (2) exchange rows k and p; scale the pivot row
+      for (int j = tid; j < n; j += blockDim.x) {
+        const double2 rk = A[k * ld + j], rp = A[p * ld + j];
+        if (p != k) A[p * ld + j] = rk;
+        A[k * ld + j] = (j == k) ? inv : cmul(rp, inv);
+      }
       __syncthreads();
-      for (int j = tid; j < n; j += blockDim.x) A[k * n + j] = (j == k) ? inv : cmul(A[k * n + j], inv);
-      __syncthreads();
-      for (int e = tid; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e - i * n;
+      // (3) eliminate column k from the other rows
+      for (int i = warp; i < n; i += NW) {
         if (i == k) continue;
-        const double2 c = col[i];
-        if (j == k) {
-          const double2 t = cmul(c, inv);
-          A[e] = make_double2(-t.x, -t.y);
-        } else {
-          const double2 t = cmul(c, A[k * n + j]);
-          A[e] = make_double2(A[e].x - t.x, A[e].y - t.y);
+        const double2 c = (i == p) ? col[k] : col[i];
+        for (int j = lane; j < n; j += 32) {
+          const double2 pr = A[k * ld + j];
+          const double2 base = (j == k) ? make_double2(0.0, 0.0) : A[i * ld + j];
+          A[i * ld + j] = make_double2(base.x - (c.x * pr.x - c.y * pr.y), base.y - (c.x * pr.y + c.y * pr.x));
         }
       }
       __syncthreads();
     }
-    for (int k = n - 1; k >= 0; --k) {
-      const int p = perm[k];
-      if (p != k) {
-        for (int i = tid; i < n; i += blockDim.x) {
-          const double2 t = A[i * n + k];
-          A[i * n + k] = A[i * n + p];
-          A[i * n + p] = t;
+    // undo the pivoting on the columns, row by row
+    for (int i = tid; i < n; i += blockDim.x) {
+      double2* r = A + (long long)i * ld;
+      for (int k = n - 1; k >= 0; --k) {
+        const int pk = perm[k];
+        if (pk != k) {
+          const double2 t = r[k];
+          r[k] = r[pk];
+          r[pk] = t;
         }
       }
-      __syncthreads();
     }
-    if (mode == INV_W) {
-      for (int e = tid; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e - i * n;
-        double2 a = A[e];
-        if (i == j) a.x -= 1.0;
-        out[it.out_off + e] = a;
-      }
-    } else if (mode == INV_DYSON_STORE) {
-      for (int e = tid; e < nn; e += blockDim.x) out[it.out_off + e] = A[e];
+    __syncthreads();
+    if (mode == INV_W || mode == INV_DYSON_STORE) {
+      for (int i = warp; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) {
+          double2 a = A[i * ld + j];
+          if (mode == INV_W && i == j) a.x -= 1.0;
+          out[it.out_off + (long long)i * n + j] = a;
+        }
     } else {
-      // Tr[G S] and Tr[(G S)^2]; thread e forms X_ij = (G S)_ij and X_ji without storing X
+      // Tr[G S] and Tr[(G S)^2]: thread (i, j) forms X_ij = (G S)_ij and X_ji without storing X
       const double2* Sb = S + it.s_off;
-      double2 s = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
-      for (int e = tid; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e - i * n;
-        double2 xij = make_double2(0.0, 0.0), xji = make_double2(0.0, 0.0);
-        for (int l = 0; l < n; ++l) {
-          xij = cfma(A[i * n + l], Sb[l * n + j], xij);
-          xji = cfma(A[j * n + l], Sb[l * n + i], xji);
+      double2 t1 = make_double2(0.0, 0.0), t2 = make_double2(0.0, 0.0);
+      for (int i = warp; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) {
+          double2 xij = make_double2(0.0, 0.0), xji = make_double2(0.0, 0.0);
+          for (int l = 0; l < n; ++l) {
+            xij = cfma(A[i * ld + l], Sb[(long long)l * n + j], xij);
+            xji = cfma(A[j * ld + l], Sb[(long long)l * n + i], xji);
+          }
+          if (i == j) t1 = cadd(t1, xij);
+          t2 = cfma(xij, xji, t2);
         }
-        if (i == j) s = cadd(s, xij);
-        s2 = cfma(xij, xji, s2);
+      for (int off = 16; off > 0; off >>= 1) {
+        t1.x += __shfl_down_sync(0xffffffffu, t1.x, off);
+        t1.y += __shfl_down_sync(0xffffffffu, t1.y, off);
+        t2.x += __shfl_down_sync(0xffffffffu, t2.x, off);
+        t2.y += __shfl_down_sync(0xffffffffu, t2.y, off);
       }
-      __shared__ double s_red2[256], s_red2i[256];
-      s_red[tid] = s.x;
-      s_redi[tid] = s.y;
-      s_red2[tid] = s2.x;
-      s_red2i[tid] = s2.y;
+      if (lane == 0) {
+        s_red[0][warp] = t1.x;
+        s_red[1][warp] = t1.y;
+        s_red[2][warp] = t2.x;
+        s_red[3][warp] = t2.y;
+      }
       __syncthreads();
-      for (int off = 128; off > 0; off >>= 1) {
-        if (tid < off) {
-          s_red[tid] += s_red[tid + off];
-          s_redi[tid] += s_redi[tid + off];
-          s_red2[tid] += s_red2[tid + off];
-          s_red2i[tid] += s_red2i[tid + off];
-        }
-        __syncthreads();
-      }
       if (tid == 0) {
-        const double2 t = cmul(it.weight, make_double2(s_red[0], s_redi[0]));
-        const double2 d = cmul(it.weight, make_double2(s_red2[0], s_red2i[0]));
-        tpart[it.slot] = make_double2(t.x, -d.x);  // (N part, dN/dmu part): dG/dmu = -G S G
+        double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+        for (int w = 0; w < NW; ++w) {
+          a.x += s_red[0][w];
+          a.y += s_red[1][w];
+          b.x += s_red[2][w];
+          b.y += s_red[3][w];
+        }
+        const double2 tn = cmul(it.weight, a);
+        const double2 td = cmul(it.weight, b);
+        tpart[it.slot] = make_double2(tn.x, -td.x);  // (N part, dN/dmu part)
       }
     }
     __syncthreads();
@@ -794,43 +808,50 @@ __global__ void __launch_bounds__(256) k_invert_warp(int mode, const InvItem* __
   }
 }
 
-void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_small_n, int nitems, int max_n,
-                         const double2* A, const double2* S, const double2* F, const double* nu, double mu,
-                         const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
-                         double2* scratch, int* status, cudaStream_t st) {
-  if (nsmall > 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpInvSmemMax);
-      attr = true;
-    }
-    const int sn = max_small_n < 1 ? 1 : max_small_n;
+void invert_plan(int mode, const InvPlan& pl, const double2* A, const double2* S, const double2* F, const double* nu,
+                 double mu, const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
+                 double2* scratch, int* status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_invert_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarpInvSmemMax);
+    cudaFuncSetAttribute(k_invert_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kInvSmemMaxN * (kInvSmemMaxN | 1) * (int)sizeof(double2));
+    attr = true;
+  }
+  const int nmid = pl.nitems - pl.nsmall - pl.nscr;
+  // the three groups are independent: when two or more are present they run on the side streams
+  // (when given) and share the GPU
+  const int ngroups = (pl.nscr > 0) + (nmid > 0) + (pl.nsmall > 0);
+  const bool fork = ngroups > 1 && pl.aux[0] != nullptr && pl.aux[1] != nullptr;
+  cudaStream_t s_mid = fork ? pl.aux[0] : st, s_small = fork ? pl.aux[1] : st;
+  if (fork) {
+    cudaEventRecord(pl.fork, st);
+    cudaStreamWaitEvent(pl.aux[0], pl.fork, 0);
+    cudaStreamWaitEvent(pl.aux[1], pl.fork, 0);
+  }
+  if (pl.nscr > 0) {  // the largest blocks first, each in a global scratch slot
+    const int grid = pl.nscr < kInvScratchSlots ? pl.nscr : kInvScratchSlots;
+    k_invert_cta<<<grid, 256, 0, st>>>(mode, pl.items + pl.nsmall, pl.nscr, pl.max_n * pl.max_n, A, S, F, nu, mu,
+                                       mu_dev, done_dev, out, trace_partial, scratch, status, 0);
+  }
+  if (nmid > 0) {
+    const size_t sm = (size_t)pl.mid_n * (pl.mid_n | 1) * sizeof(double2);
+    k_invert_cta<<<nmid, 256, sm, s_mid>>>(mode, pl.items + pl.nsmall + pl.nscr, nmid, 0, A, S, F, nu, mu, mu_dev,
+                                           done_dev, out, trace_partial, nullptr, status, 1);
+  }
+  if (pl.nsmall > 0) {
+    const int sn = pl.small_n < 1 ? 1 : pl.small_n;
     const size_t per_warp = (size_t)(mode == INV_DYSON_TRACE ? 2 : 1) * sn * (sn + 1) * sizeof(double2);
     const int wpc = 8 * per_warp <= (size_t)kWarpInvSmemMax ? 8 : 4;  // 4 x 2 x 32 x 33 x 16 B fits
-    k_invert_warp<<<(nsmall + wpc - 1) / wpc, 32 * wpc, wpc * per_warp, st>>>(
-        mode, items, nsmall, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial, status, sn);
+    k_invert_warp<<<(pl.nsmall + wpc - 1) / wpc, 32 * wpc, wpc * per_warp, s_small>>>(
+        mode, pl.items, pl.nsmall, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial, status, sn);
   }
-  if (nitems > nsmall)
-    invert_blocks(mode, items + nsmall, nitems - nsmall, max_n, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial,
-                  scratch, status, st);
-}
-
-void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
-                   const double2* F, const double* nu, double mu, const double* mu_dev, const double* done_dev,
-                   double2* out, double2* trace_partial, double2* scratch, int* status, cudaStream_t st) {
-  if (nitems <= 0) return;
-  const int use_smem = max_n <= kInvSmemMaxN ? 1 : 0;
-  const size_t sm = use_smem ? (size_t)max_n * max_n * sizeof(double2) : 0;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kInvSmemMaxN * kInvSmemMaxN * (int)sizeof(double2));
-    attr_set = true;
+  if (fork) {
+    cudaEventRecord(pl.join[0], pl.aux[0]);
+    cudaEventRecord(pl.join[1], pl.aux[1]);
+    cudaStreamWaitEvent(st, pl.join[0], 0);
+    cudaStreamWaitEvent(st, pl.join[1], 0);
   }
-  int grid = nitems;
-  if (!use_smem && grid > 304) grid = 304;  // one scratch slot per resident CTA
-  k_invert<<<grid, 256, sm, st>>>(mode, items, nitems, max_n, A, S, F, nu, mu, mu_dev, done_dev, out, trace_partial,
-                                  scratch, status, use_smem);
 }
 
 // ---------------------------------------------------------------------------

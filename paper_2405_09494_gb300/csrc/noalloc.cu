@@ -72,8 +72,8 @@ extern "C" SGW_API sgw_status sgw_screened_interaction_noalloc(sgw_ctx* c, const
   double2* Pw = scr + (size_t)c->nwb * pe;  // [nw_b][p_elems], fully overwritten below
   const double2 one = make_double2(1.0, 0.0);
   series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, one, 0, st);
-  invert_blocks_split(INV_W, c->d_w_items, c->n_w_small, c->w_small_n, c->n_w_items, c->max_aux_block, P0w, nullptr,
-                      nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, nullptr, c->d_status, st);
+  invert_plan(INV_W, c->w_plan, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, nullptr, c->d_status,
+              st);
   series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, one, 0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -108,14 +108,19 @@ struct InvItem {
   double2 weight;    // trace weight (Dyson number mode): partial = (Re weight Tr[G S], -Re weight Tr[G S G S])
 };
 enum InvMode { INV_W = 0, INV_DYSON_STORE = 1, INV_DYSON_TRACE = 2 };
-void invert_blocks(int mode, const InvItem* items, int nitems, int max_n, const double2* A, const double2* S,
-                   const double2* F, const double* nu, double mu, const double* mu_dev, const double* done_dev,
-                   double2* out, double2* trace_partial, double2* scratch, int* status, cudaStream_t st);
-// items [0, nsmall) have n <= 32 (one warp each), the rest run one CTA each
-void invert_blocks_split(int mode, const InvItem* items, int nsmall, int max_small_n, int nitems, int max_n,
-                         const double2* A, const double2* S, const double2* F, const double* nu, double mu,
-                         const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
-                         double2* scratch, int* status, cudaStream_t st);
+// A batch of blocks split three ways, each group ordered by n, largest first:
+// items [0, nsmall) have n <= 32 (one warp each, largest n small_n); [nsmall, nsmall + nscr)
+// n > 90 (one CTA each, global scratch slots of max_n^2); the rest 32 < n <= 90 (one CTA each,
+// shared memory, largest n mid_n).  With both side streams set, the groups run concurrently.
+struct InvPlan {
+  const InvItem* items = nullptr;
+  int nitems = 0, nsmall = 0, small_n = 1, nscr = 0, mid_n = 1, max_n = 1;
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+};
+void invert_plan(int mode, const InvPlan& plan, const double2* A, const double2* S, const double2* F, const double* nu,
+                 double mu, const double* mu_dev, const double* done_dev, double2* out, double2* trace_partial,
+                 double2* scratch, int* status, cudaStream_t st);
 void mu_start(double* s, double start_host, const double* start_dev, double lo, double hi, cudaStream_t st);
 void mu_update(double* s, const double2* partial, int n, double target, double tol, cudaStream_t st);
 
@@ -234,7 +239,10 @@ struct sgw_ctx {
   // static launch tables of the hot path (built once, so the iteration can be captured in a graph)
   bool tables = false;
   sgw::InvItem *d_w_items = nullptr, *d_dy_items = nullptr;
-  int n_w_items = 0, n_dy_items = 0, n_w_small = 0, n_dy_small = 0, w_small_n = 1, dy_small_n = 1;
+  int n_w_items = 0, n_dy_items = 0;
+  sgw::InvPlan w_plan, dy_plan;   // W solve and Dyson batches (items above, side streams below)
+  cudaStream_t inv_aux[2] = {nullptr, nullptr};
+  cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
   // iteration buffers and the captured graph
   double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
