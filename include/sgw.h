@@ -208,7 +208,11 @@ SGW_API sgw_status sgw_g0(sgw_ctx* ctx, double* mu_out, void* G_tau, sgw_stream 
 /* a2 + a3: P0^q(tau) for every wedge q from G(tau) (Eq. (P0), Algorithm 3):
  * G of every point of the zone is read through the star map (no unfolding),
  * X_Q = G^k(-tau) V_Q G^{k+q}(tau), P0 += X V^dagger over the diagonal
- * auxiliary blocks.  G_tau packed [ntau][g_elems]; P0_tau packed [ntau][p_elems]. */
+ * auxiliary blocks.  G_tau packed [ntau][g_elems]; P0_tau packed [ntau][p_elems].
+ * Each block of P0 is Hermitian when G^k(tau) is Hermitian and the two loaded
+ * orientations of V satisfy V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger: only the tiles
+ * on and above the diagonal are contracted and the strict lower triangle is
+ * written as the conjugate transpose of the upper one. */
 SGW_API sgw_status sgw_polarization(sgw_ctx* ctx, const void* G_tau, void* P0_tau, sgw_stream stream);
 /* a4 + a5 + a6: P0(tau) -> P0(i Omega) -> P = [I - P0]^{-1} P0 per block
  * (Eq. (P02P), FP64 in both forms) -> P(tau). */

@@ -145,14 +145,16 @@ static BdGeom geom(int U, int Vd, int Wd, int left, int trans, int conj, int acc
 
 // Gram units/tiles for one output block family.  out block of size nb at out_off (ld nb);
 // A rows start at a_off (+ row * a_row), B rows at b_off; pairs [0, npair) with strides.
+// With herm, the output block is Hermitian: tiles strictly below the diagonal are left out (the
+// caller fills them by conjugate transposition).
 static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& tiles, long long unit_base, int nb,
                            long long out_off, long long a_off, long long b_off, long long a_row, long long b_row,
-                           int npair, long long kwork, long long target = (1LL << 20)) {
+                           int npair, long long kwork, long long target = (1LL << 20), bool herm = false) {
   // balanced square tiles of at most 32 rows
   const int nt_side = (nb + 31) / 32;
   const int ts = (nb + nt_side - 1) / nt_side;
   for (int tm = 0; tm < nb; tm += ts)
-    for (int tn = 0; tn < nb; tn += ts) {
+    for (int tn = herm ? tm : 0; tn < nb; tn += ts) {
       const int rm = std::min(ts, nb - tm), rn = std::min(ts, nb - tn);
       long long per_pair = (long long)rm * rn * kwork;
       long long chunk = std::max(1LL, target / std::max(1LL, per_pair));
@@ -295,7 +297,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
-  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
+  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab); dfree(c->d_herm_items);
   for (auto& a : c->inv_aux)
     if (a) cudaStreamDestroy(a);
   for (auto& e : c->inv_ev)
@@ -672,6 +674,23 @@ extern "C" SGW_API sgw_status sgw_g0(sgw_ctx* c, double* mu_out, void* G_tau, sg
 // ---------------------------------------------------------------------------
 // a3: polarization
 // ---------------------------------------------------------------------------
+// P0^q(tau) is Hermitian block by block (Eq. (P0) with V^{k+q,k}(Q) = V^{k,k+q}(Q)^dagger and
+// Hermitian G^k(tau)); the Gram stages compute tiles on and above the diagonal and this fills the
+// strict lower triangle of every auxiliary block at every tau by conjugate transposition.
+sgw_status sgw::p0_lower_from_upper(sgw_ctx* c, double2* P0, cudaStream_t st) {
+  if (!c->d_herm_items) {
+    std::vector<HermItem> h;
+    for (int t = 0; t < c->nt; ++t)
+      for (size_t b = 0; b < c->auxb_off.size(); ++b)
+        if (c->auxb_n[b] > 1) h.push_back({(long long)t * c->p_elems + c->auxb_off[b], c->auxb_n[b], 0});
+    c->n_herm_items = (int)h.size();
+    if (h.empty()) return SGW_OK;
+    CKS(upload(c, c->d_herm_items, h));
+  }
+  run(c, "p0_mirror", 0.0, 1, st, [&] { hermitian_fill(c->d_herm_items, c->n_herm_items, P0, st); });
+  return SGW_OK;
+}
+
 static sgw_status build_p0_plan(sgw_ctx* c) {
   ContractionPlan& P = c->plan_p0;
   if (P.built) return SGW_OK;
@@ -728,7 +747,7 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->p_elems + c->auxb_off[b],
                      (p0 * nc + tl) * vs + (long long)st * nao * nao, p0 * vs + (long long)st * nao * nao,
-                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target);
+                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target, true);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
@@ -745,7 +764,9 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
     P.fl_A_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     P.fl_B_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
-  for (int w = 0; w < nw; ++w) P.fl_G_t += 8.0 * Nk * (double)nao * nao * c->part_aux[w].elems;
+  // the Gram stage needs the upper triangles of the Hermitian blocks only
+  for (size_t b = 0; b < c->auxb_n.size(); ++b)
+    P.fl_G_t += 8.0 * Nk * (double)nao * nao * 0.5 * c->auxb_n[b] * (c->auxb_n[b] + 1.0);
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_B, B));
   CKS(upload(c, P.d_units, units));
@@ -794,6 +815,7 @@ static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2*
     run(c, t_gram.c_str(), P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X, V, P.d_units + u0, (int)(u1 - u0), part, st); });
     run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(alpha), 0, st); });
   }
+  CKS(p0_lower_from_upper(c, out, st));
   return SGW_OK;
 }
 
@@ -862,14 +884,16 @@ static sgw_status ensure_tables(sgw_ctx* c) {
   const int wG = c->rep[0];
   for (int w = 0; w < c->nwedge; ++w) tab[3 * nb + w] = ((long long)wG * c->Nk + c->wedge_k[w]) * vs;
   // three groups (warp-sized blocks, blocks above 90 in global scratch, the rest in shared
-  // memory), each ordered largest first so the longest eliminations start first; slots keep the
-  // original order so the trace partials are summed in a fixed order
+  // memory); the two CTA groups ordered largest first so the longest eliminations start first,
+  // the warp group left in frequency order (eight warps of a CTA share one SM's FP64 pipe, so
+  // its CTAs are best mixed in size); slots keep the original order so the trace partials are
+  // summed in a fixed order
   auto group = [](const InvItem& x) { return x.n <= 32 ? 0 : x.n > 90 ? 1 : 2; };
   auto split = [&](std::vector<InvItem>& v, InvPlan& pl) {
     for (size_t i = 0; i < v.size(); ++i) v[i].slot = (int)i;
     std::stable_sort(v.begin(), v.end(), [&](const InvItem& a, const InvItem& b) {
       const int ga = group(a), gb = group(b);
-      return ga != gb ? ga < gb : a.n > b.n;
+      return ga != gb ? ga < gb : (ga != 0 && a.n > b.n);
     });
     pl = InvPlan();
     pl.nitems = (int)v.size();

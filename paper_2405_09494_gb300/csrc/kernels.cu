@@ -472,6 +472,22 @@ void to_c64(const double2* a, float2* b, long long n, cudaStream_t st) {
   if (n > 0) k_to_c64<<<grid_for(n, 256, 8192), 256, 0, st>>>(a, b, n);
 }
 
+// strict lower triangle of each block from its upper triangle: one CTA per block, rows over
+// warps, columns over lanes (reads above the diagonal, writes below it: no overlap)
+__global__ void __launch_bounds__(256) k_hermitian_fill(const HermItem* __restrict__ items, double2* __restrict__ out) {
+  const HermItem it = items[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double2* B = out + it.off;
+  for (int i = warp + 1; i < it.n; i += 8)
+    for (int j = lane; j < i; j += 32) {
+      const double2 u = B[(long long)j * it.n + i];
+      B[(long long)i * it.n + j] = make_double2(u.x, -u.y);
+    }
+}
+void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_t st) {
+  if (nitems > 0) k_hermitian_fill<<<nitems, 256, 0, st>>>(items, out);
+}
+
 // ---------------------------------------------------------------------------
 // Series map along the tau / frequency axis: out[m][e] = alpha sum_t T[m][t] in[t][e].
 // ---------------------------------------------------------------------------

@@ -91,6 +91,12 @@ void gram_partials(const GramGeom& g, const float2* A, const float2* B, const Gr
 void gram_reduce(const GramTile* tiles, int ntiles, const float2* partial, double2* out, double2 alpha, int accumulate,
                  cudaStream_t st);
 void to_c64(const double2* a, float2* b, long long n, cudaStream_t st);
+// Hermitian blocks: out[off + i n + j] = conj(out[off + j n + i]) for i > j.
+struct HermItem {
+  long long off;
+  int n, pad;
+};
+void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_t st);
 
 // out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
 void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,
@@ -244,6 +250,8 @@ struct sgw_ctx {
   cudaStream_t inv_aux[2] = {nullptr, nullptr};
   cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
+  sgw::HermItem* d_herm_items = nullptr;  // P0 blocks at every tau (lower triangles from upper)
+  int n_herm_items = 0;
   // iteration buffers and the captured graph
   double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
   double* h_pinned = nullptr;  // host-visible scalars written at the end of a captured iteration
@@ -310,6 +318,8 @@ inline void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
   cudaEventRecord(b, st);
   c->prof_pending.push_back({id, a, b});
 }
+
+sgw_status p0_lower_from_upper(sgw_ctx* c, double2* P0, cudaStream_t st);
 
 // tensor-core chains of the chosen form (tc.cu)
 bool tc_supported(const sgw_ctx* c);

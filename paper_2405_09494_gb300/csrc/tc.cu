@@ -814,25 +814,35 @@ std::vector<KRange> split_k(int nslab, int nchunk, long long target) {
 // values of a chunk against the same B rows.  Rows [r0, r0 + nr) of A against B rows
 // [b_y, b_y + ncols) in tiles of 128 x ntile, ordered K range first (the tiles of one K range run
 // side by side and share their loads in L2).  Appends the jobs.
+// With herm (a Hermitian output whose A rows and B columns index the same range), tiles whose
+// rows all lie below their columns are left out; the caller fills them by conjugate transposition.
 struct GramTiles {
   long long first;     // first unit (relative to the chunk's first unit)
   int count, stride;   // units per tile, unit stride between the K ranges of one tile
   int mts, nts, rpt, ntile;
+  std::vector<int> index;  // [mi * nts + ni]: unit of the tile within a K range, -1 when left out
 };
 GramTiles gram_interleaved(std::vector<TcJob>& jobs, long long slot0, long long slot, const TcJob& proto, int r0,
-                           int nr, int nc, int ncols, int ntile, int nslab, int nchunk, long long unit) {
+                           int nr, int nc, int ncols, int ntile, int nslab, int nchunk, long long unit,
+                           bool herm = false) {
   GramTiles g;
   g.rpt = 128 / nc;
   g.ntile = ntile;
   g.mts = (nr + g.rpt - 1) / g.rpt;
   g.nts = (ncols + ntile - 1) / ntile;
+  g.index.assign((size_t)g.mts * g.nts, -1);
+  int kept = 0;
+  for (int mi = 0; mi < g.mts; ++mi)
+    for (int ni = 0; ni < g.nts; ++ni)
+      if (!(herm && mi * g.rpt >= ntile * (ni + 1))) g.index[(size_t)mi * g.nts + ni] = kept++;
   const std::vector<KRange> kr = split_k(nslab, nchunk, unit);
   g.first = (long long)jobs.size() - slot0;
   g.count = (int)kr.size();
-  g.stride = g.mts * g.nts;
+  g.stride = kept;
   for (const KRange& r : kr)
     for (int mi = 0; mi < g.mts; ++mi)
       for (int ni = 0; ni < g.nts; ++ni) {
+        if (g.index[(size_t)mi * g.nts + ni] < 0) continue;
         TcJob j = proto;
         j.a_y = (r0 + mi * g.rpt) * nc;
         j.m_rows = std::min(g.rpt, nr - mi * g.rpt) * nc;
@@ -861,6 +871,8 @@ void gram_out_tiles(std::vector<TcTile>& tiles, const GramTiles& g, int r0, int 
     const int a0 = std::max(ra0, tr0), a1 = std::min(ra0 + nra, tr1);
     if (a0 >= a1) continue;
     for (int ni = 0; ni < g.nts; ++ni) {
+      const int idx = g.index[(size_t)mi * g.nts + ni];
+      if (idx < 0) continue;
       const int tc0 = cb0 + ni * g.ntile, tc1 = tc0 + g.ntile;
       const int b0 = std::max(ca0, tc0), b1 = std::min(ca0 + nca, tc1);
       if (b0 >= b1) continue;
@@ -872,7 +884,7 @@ void gram_out_tiles(std::vector<TcTile>& tiles, const GramTiles& g, int r0, int 
       t.pm0 = (a0 - tr0) * nc + tl;
       t.pm_stride = nc;
       t.pn0 = b0 - tc0;
-      t.unit_begin = (int)(g.first + mi * g.nts + ni);
+      t.unit_begin = (int)(g.first + idx);
       t.unit_count = g.count;
       t.unit_stride = g.stride;
       tiles.push_back(t);
@@ -979,7 +991,7 @@ static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
       TcJob j{};
       j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
       j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit);
+      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit, true);
       for (int t = t0; t < t1; ++t)
         gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
     }
@@ -1040,7 +1052,9 @@ static sgw_status build_p0(sgw_ctx* c) {
     T.fl_vg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     T.fl_gvg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
-  for (int w = 0; w < nw; ++w) T.fl_pg += 8.0 * Nk * (double)nao * nao * c->part_aux[w].elems;
+  // the Gram stage needs the upper triangles of the Hermitian blocks only
+  for (size_t b = 0; b < c->auxb_n.size(); ++b)
+    T.fl_pg += 8.0 * Nk * (double)nao * nao * 0.5 * c->auxb_n[b] * (c->auxb_n[b] + 1.0);
   CKS(up(c, T.d_vg, vg));
   CKS(up(c, T.d_gvg, gvg));
   T.built_p0 = true;
@@ -1305,7 +1319,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
     run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
   if (tune) T.tuned_p0 = true;
-  return SGW_OK;
+  return p0_lower_from_upper(c, out, st);
 }
 
 sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, cudaStream_t st) {
