@@ -150,8 +150,10 @@ static BdGeom geom(int U, int Vd, int Wd, int left, int trans, int conj, int acc
 static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& tiles, long long unit_base, int nb,
                            long long out_off, long long a_off, long long b_off, long long a_row, long long b_row,
                            int npair, long long kwork, long long target = (1LL << 20), bool herm = false) {
-  // balanced square tiles of at most 32 rows
-  const int nt_side = (nb + 31) / 32;
+  // balanced square tiles of at most 32 rows (16 for a Hermitian block: finer tiles leave out
+  // more of the lower triangle, and small tiles keep every lane busy by splitting K)
+  const int cap = herm ? 16 : 32;
+  const int nt_side = (nb + cap - 1) / cap;
   const int ts = (nb + nt_side - 1) / nt_side;
   for (int tm = 0; tm < nb; tm += ts)
     for (int tn = herm ? tm : 0; tn < nb; tn += ts) {

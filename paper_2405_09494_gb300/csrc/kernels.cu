@@ -81,6 +81,12 @@ __device__ __forceinline__ double negd(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
 }
 __device__ __forceinline__ float negd(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
+template <typename Z>
+__device__ __forceinline__ Z make_neg(Z a) {
+  a.x = negd(a.x);
+  a.y = negd(a.y);
+  return a;
+}
 // scale class by bit pattern: 0 = +1, 1 = -1, 2 = general
 __device__ __forceinline__ int scale_kind(double2 s) {
   const long long xb = __double_as_longlong(s.x), yb = __double_as_longlong(s.y);
@@ -106,10 +112,30 @@ __global__ void __launch_bounds__(256) k_bd_mult(BdGeom g, const Z* __restrict__
     const int* bz = pz + (long long)item.part * g.n_part;
     const long long* bd = pd + (long long)item.part * g.n_part;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-      const int u = e / VW;
-      const int r = e - u * VW;
-      const int v = r / g.Wd;
-      const int w = r - v * g.Wd;
+      // block-major output order: the outputs that use one diagonal block of M are consecutive,
+      // so the lanes of a warp share one block size and run loops of equal length
+      int u, v, w;
+      if (LEFT) {
+        // block of rows [st, st + n): outputs (u, v, w) with w fastest, then v, then u
+        const int UW = g.U * g.Wd;
+        const int cs = e / UW;  // a row of the block holding output e
+        const int st = bs[cs], n = bz[cs];
+        const int r2 = e - st * UW;
+        u = r2 / (n * g.Wd);
+        const int rem = r2 - u * n * g.Wd;
+        const int lv = rem / g.Wd;
+        v = st + lv;
+        w = rem - lv * g.Wd;
+      } else {
+        // block of columns [st, st + n): outputs (u, v, w) with w fastest, then v (per u)
+        u = e / VW;
+        const int r = e - u * VW;
+        const int cs = r / g.Vd;  // a column of the block holding output r
+        const int st = bs[cs], n = bz[cs];
+        const int r2 = r - st * g.Vd;
+        v = r2 / n;
+        w = st + (r2 - v * n);
+      }
       Z acc = czero<Z>();
       if (LEFT) {
         const int st = bs[v], n = bz[v];
@@ -199,6 +225,7 @@ __global__ void __launch_bounds__(256) k_bd_mult2(BdGeom g, const Z* __restrict_
                                                   int ustride) {
   for (long long it = blockIdx.y; it < nitems; it += gridDim.y) {
     const BdItem item = items[it];
+    const int sk = scale_kind(item.scale);
     const int nu = nunits[item.part];
     const int4* up = units + (long long)item.part * ustride;
     const long long* dp = udoff + (long long)item.part * ustride;
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(256) k_bd_mult2(BdGeom g, const Z* __restrict_
 #pragma unroll
         for (int l = 0; l < kChunk; ++l)
           if (l < un.y) {
-            Z r = cmul(sc, acc[l]);
+            Z r = sk == 0 ? acc[l] : sk == 1 ? make_neg(acc[l]) : cmul(sc, acc[l]);
             if (g.accumulate) r = cadd(yr[l], r);
             yr[l] = r;
           }
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(256) k_bd_mult2(BdGeom g, const Z* __restrict_
 #pragma unroll
         for (int l = 0; l < kChunk; ++l)
           if (l < un.y) {
-            Z rr = cmul(sc, acc[l]);
+            Z rr = sk == 0 ? acc[l] : sk == 1 ? make_neg(acc[l]) : cmul(sc, acc[l]);
             if (g.accumulate) rr = cadd(yc[(long long)l * g.ys_v], rr);
             yc[(long long)l * g.ys_v] = rr;
           }
