@@ -150,25 +150,26 @@ static BdGeom geom(int U, int Vd, int Wd, int left, int trans, int conj, int acc
 static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& tiles, long long unit_base, int nb,
                            long long out_off, long long a_off, long long b_off, long long a_row, long long b_row,
                            int npair, long long kwork, long long target = (1LL << 20), bool herm = false) {
-  // balanced square tiles of at most 32 rows (16 for a Hermitian block: finer tiles leave out
-  // more of the lower triangle, and small tiles keep every lane busy by splitting K)
-  const int cap = herm ? 16 : 32;
-  const int nt_side = (nb + cap - 1) / cap;
+  // balanced square tiles of at most 32 rows; in a Hermitian block the diagonal tiles contract
+  // only their elements on and above the diagonal
+  const int nt_side = (nb + 31) / 32;
   const int ts = (nb + nt_side - 1) / nt_side;
   for (int tm = 0; tm < nb; tm += ts)
     for (int tn = herm ? tm : 0; tn < nb; tn += ts) {
       const int rm = std::min(ts, nb - tm), rn = std::min(ts, nb - tn);
-      long long per_pair = (long long)rm * rn * kwork;
+      long long per_pair = (long long)rm * rn * kwork / (herm && tm == tn ? 2 : 1);
       long long chunk = std::max(1LL, target / std::max(1LL, per_pair));
       if (chunk > npair) chunk = npair;
       // spread the pairs evenly over the units of this tile
       const long long nun = (npair + chunk - 1) / chunk;
       chunk = (npair + nun - 1) / nun;
+      const int tri = herm && tm == tn ? 1 : 0;
       GramTile t;
       t.out_off = out_off + (long long)tm * nb + tn;
       t.ld = nb;
       t.rows_m = rm;
       t.rows_n = rn;
+      t.tri = tri;
       t.unit_begin = (int)((long long)units.size() - unit_base);
       int cnt = 0;
       for (long long r0 = 0; r0 < npair; r0 += chunk) {
@@ -180,7 +181,7 @@ static void add_gram_block(std::vector<GramUnit>& units, std::vector<GramTile>& 
         u.a_off = a_off + (long long)tm * a_row;
         u.b_off = b_off + (long long)tn * b_row;
         u.slot = (int)((long long)units.size() - unit_base);
-        u.pad = 0;
+        u.tri = tri;
         units.push_back(u);
         ++cnt;
       }
@@ -1201,6 +1202,7 @@ static sgw_status build_k_plan(sgw_ctx* c) {
   const int wG = c->rep[0];
   for (int A0 = 0; A0 < c->naux; A0 += 32) {
     GramTile t;
+    t.tri = 0;
     t.out_off = A0;
     t.ld = 32;
     t.rows_m = 1;
@@ -1216,7 +1218,7 @@ static sgw_status build_k_plan(sgw_ctx* c) {
       u.a_off = (long long)c->rep[kp] * nao * nao;
       u.b_off = ((long long)wG * Nk + kp) * vs + (long long)A0 * nao * nao;
       u.slot = (int)ru.size();
-      u.pad = 0;
+      u.tri = 0;
       ru.push_back(u);
     }
     rt.push_back(t);

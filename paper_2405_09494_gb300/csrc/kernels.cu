@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __re
   const int rmax = u.rows_m > u.rows_n ? u.rows_m : u.rows_n;
   const int KC = gram_chunk(rmax);
   const int LD = KC + 1;
-  const int mn = u.rows_m * u.rows_n;
+  const bool tri = u.tri != 0;  // square diagonal tile of a Hermitian block: elements i <= j only
+  const int mn = tri ? u.rows_m * (u.rows_m + 1) / 2 : u.rows_m * u.rows_n;
   // Every lane works on a real output: up to 4 outputs per thread for large tiles,
   // K split over P phases for small ones.  No padded rows are ever multiplied.
   const int P = mn >= 256 ? 1 : 256 / mn;
@@ -367,9 +368,20 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __re
   int em[4], en[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int e = (mn >= 256 ? tid + 256 * i : tid % mn);
-    em[i] = e / u.rows_n;
-    en[i] = e - em[i] * u.rows_n;
+    int e = (mn >= 256 ? tid + 256 * i : tid % mn);
+    if (tri) {
+      // row-major upper triangle: row r holds rows_m - r elements
+      int r = 0;
+      while (r < u.rows_m - 1 && e >= u.rows_m - r) {
+        e -= u.rows_m - r;
+        ++r;
+      }
+      em[i] = r;
+      en[i] = r + e < u.rows_m ? r + e : u.rows_m - 1;
+    } else {
+      em[i] = e / u.rows_n;
+      en[i] = e - em[i] * u.rows_n;
+    }
   }
   Z acc[4];
 #pragma unroll
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __re
       }
       __syncthreads();
       const int kend = (K - k0) < KC ? (K - k0) : KC;
-      if (std::is_same<Z, float2>::value && mn >= 256) {
+      if (std::is_same<Z, float2>::value && mn >= 256 && !tri) {
         // single precision: 2x2 register tile (rows ty, ty+16; columns tx, tx+16) halves the shared loads
         const int ty = tid >> 4, tx = tid & 15;
         const bool m0 = ty < u.rows_m, m1 = ty + 16 < u.rows_m, n0 = tx < u.rows_n, n1 = tx + 16 < u.rows_n;
@@ -427,7 +439,7 @@ __global__ void __launch_bounds__(256) k_gram_partials(GramGeom g, const Z* __re
     }
   }
   Z* out = partial + (long long)u.slot * 1024;
-  if (std::is_same<Z, float2>::value && mn >= 256) {
+  if (std::is_same<Z, float2>::value && mn >= 256 && !tri) {
     const int ty = tid >> 4, tx = tid & 15;
     if (ty < u.rows_m && tx < u.rows_n) out[ty * 32 + tx] = acc[0];
     if (ty < u.rows_m && tx + 16 < u.rows_n) out[ty * 32 + tx + 16] = acc[1];
@@ -455,6 +467,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const GramTile* __restrict_
   const GramTile t = tiles[blockIdx.x];
   for (int e = threadIdx.x; e < t.rows_m * t.rows_n; e += blockDim.x) {
     const int i = e / t.rows_n, j = e - i * t.rows_n;
+    if (t.tri && i > j) continue;  // below the diagonal of a Hermitian block: filled by transposition
     double2 s = make_double2(0, 0);
     for (int q = 0; q < t.unit_count; ++q) {
       const Z p = partial[(long long)(t.unit_begin + q) * 1024 + i * 32 + j];

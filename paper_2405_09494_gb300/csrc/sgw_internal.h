@@ -43,7 +43,7 @@ struct GramUnit {
   int rows_m, rows_n;      // tile extent
   int r0, r1;              // pair range [r0, r1)
   int slot;                // partial-sum slot (units run largest first; tiles address slots)
-  int pad;
+  int tri;                 // 1: diagonal tile of a Hermitian block, only elements i <= j
 };
 
 // Output tile of a Gram reduction: sums its units (in order) into the packed output.
@@ -52,6 +52,7 @@ struct GramTile {
   int ld;             // row stride of the output block
   int rows_m, rows_n;
   int unit_begin, unit_count;
+  int tri;            // 1: only elements i <= j are reduced (the rest is filled by transposition)
 };
 
 // Kernel launchers (kernels.cu).
