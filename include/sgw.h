@@ -210,9 +210,12 @@ SGW_API sgw_status sgw_g0(sgw_ctx* ctx, double* mu_out, void* G_tau, sgw_stream 
  * X_Q = G^k(-tau) V_Q G^{k+q}(tau), P0 += X V^dagger over the diagonal
  * auxiliary blocks.  G_tau packed [ntau][g_elems]; P0_tau packed [ntau][p_elems].
  * Each block of P0 is Hermitian when G^k(tau) is Hermitian and the two loaded
- * orientations of V satisfy V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger: only the tiles
- * on and above the diagonal are contracted and the strict lower triangle is
- * written as the conjugate transpose of the upper one. */
+ * orientations of V satisfy V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger.  When both
+ * Matsubara sets given to sgw_create are closed under w -> -w (fermionic n ->
+ * -n-1, bosonic n -> -n; the transforms then keep Hermiticity exactly), only
+ * the tiles on and above the diagonal are contracted and the strict lower
+ * triangle is written as the conjugate transpose of the upper one (here and in
+ * sgw_self_energy); otherwise every tile is contracted. */
 SGW_API sgw_status sgw_polarization(sgw_ctx* ctx, const void* G_tau, void* P0_tau, sgw_stream stream);
 /* a4 + a5 + a6: P0(tau) -> P0(i Omega) -> P = [I - P0]^{-1} P0 per block
  * (Eq. (P02P), FP64 in both forms) -> P(tau). */

@@ -250,6 +250,16 @@ extern "C" SGW_API sgw_status sgw_create(const sgw_params* p, sgw_ctx** out) {
   c->p = *p;
   c->mats_f.assign(p->mats_f, p->mats_f + p->nw_f);
   c->mats_b.assign(p->mats_b, p->mats_b + p->nw_b);
+  {
+    // with frequency sets closed under w -> -w, G(tau), P0(tau), P(tau) and Sigma~(tau) keep the
+    // Hermiticity of their inputs exactly, and the Gram stages may use it
+    auto closed = [](const std::vector<int>& v, int shift) {
+      for (int n : v)
+        if (std::find(v.begin(), v.end(), -n - shift) == v.end()) return false;
+      return true;
+    };
+    c->herm = closed(c->mats_f, 1) && closed(c->mats_b, 0);
+  }
   c->p.mats_f = c->mats_f.data();
   c->p.mats_b = c->mats_b.data();
   c->Nk = p->nk[0] * p->nk[1] * p->nk[2];
@@ -300,7 +310,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
-  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab); dfree(c->d_herm_items);
+  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab); dfree(c->d_herm_items[0]); dfree(c->d_herm_items[1]);
   for (auto& a : c->inv_aux)
     if (a) cudaStreamDestroy(a);
   for (auto& e : c->inv_ev)
@@ -677,20 +687,31 @@ extern "C" SGW_API sgw_status sgw_g0(sgw_ctx* c, double* mu_out, void* G_tau, sg
 // ---------------------------------------------------------------------------
 // a3: polarization
 // ---------------------------------------------------------------------------
-// P0^q(tau) is Hermitian block by block (Eq. (P0) with V^{k+q,k}(Q) = V^{k,k+q}(Q)^dagger and
-// Hermitian G^k(tau)); the Gram stages compute tiles on and above the diagonal and this fills the
-// strict lower triangle of every auxiliary block at every tau by conjugate transposition.
-sgw_status sgw::p0_lower_from_upper(sgw_ctx* c, double2* P0, cudaStream_t st) {
-  if (!c->d_herm_items) {
+// With Hermitian G^k(tau) and V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger, every block of P0^q(tau)
+// (Eq. (P0)) is Hermitian, and with it P^q(tau) and Sigma~^k(tau) (Eqs. (P02P), (sigma)) when
+// the frequency sets are closed under w -> -w (c->herm).  The Gram stages then contract only the
+// tiles on and above the diagonal, and this fills the strict lower triangle of every block of the
+// family (which = 0: Sigma~, orbital blocks; 1: P0, auxiliary blocks) at every tau by conjugate
+// transposition.  Without c->herm the Gram stages contract every tile and nothing is filled.
+double sgw::gram_elems(const sgw_ctx* c, int nb) { return c->herm ? 0.5 * nb * (nb + 1.0) : (double)nb * nb; }
+
+sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st) {
+  if (!c->herm) return SGW_OK;
+  HermItem*& d = c->d_herm_items[which];
+  int& n = c->n_herm_items[which];
+  if (!d) {
+    const auto& off = which == 0 ? c->aob_off : c->auxb_off;
+    const auto& sz = which == 0 ? c->aob_n : c->auxb_n;
+    const long long elems = which == 0 ? c->g_elems : c->p_elems;
     std::vector<HermItem> h;
     for (int t = 0; t < c->nt; ++t)
-      for (size_t b = 0; b < c->auxb_off.size(); ++b)
-        if (c->auxb_n[b] > 1) h.push_back({(long long)t * c->p_elems + c->auxb_off[b], c->auxb_n[b], 0});
-    c->n_herm_items = (int)h.size();
+      for (size_t b = 0; b < off.size(); ++b)
+        if (sz[b] > 1) h.push_back({(long long)t * elems + off[b], sz[b], 0});
+    n = (int)h.size();
     if (h.empty()) return SGW_OK;
-    CKS(upload(c, c->d_herm_items, h));
+    CKS(upload(c, d, h));
   }
-  run(c, "p0_mirror", 0.0, 1, st, [&] { hermitian_fill(c->d_herm_items, c->n_herm_items, P0, st); });
+  run(c, which == 0 ? "sigma_mirror" : "p0_mirror", 0.0, 1, st, [&] { hermitian_fill(d, n, X, st); });
   return SGW_OK;
 }
 
@@ -750,7 +771,7 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->p_elems + c->auxb_off[b],
                      (p0 * nc + tl) * vs + (long long)st * nao * nao, p0 * vs + (long long)st * nao * nao,
-                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target, true);
+                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target, c->herm);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
@@ -767,9 +788,9 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
     P.fl_A_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     P.fl_B_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
-  // the Gram stage needs the upper triangles of the Hermitian blocks only
+  // with Hermitian blocks the Gram stage needs their upper triangles only
   for (size_t b = 0; b < c->auxb_n.size(); ++b)
-    P.fl_G_t += 8.0 * Nk * (double)nao * nao * 0.5 * c->auxb_n[b] * (c->auxb_n[b] + 1.0);
+    P.fl_G_t += 8.0 * Nk * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_B, B));
   CKS(upload(c, P.d_units, units));
@@ -818,7 +839,7 @@ static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2*
     run(c, t_gram.c_str(), P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X, V, P.d_units + u0, (int)(u1 - u0), part, st); });
     run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(alpha), 0, st); });
   }
-  CKS(p0_lower_from_upper(c, out, st));
+  CKS(lower_from_upper(c, 1, out, st));
   return SGW_OK;
 }
 
@@ -1031,7 +1052,7 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->g_elems + c->aob_off[b],
                      (p0 * nc + tl) * vs + (long long)st * nao, p0 * vs + (long long)st * nao, nao, nao, Nk,
-                     (long long)c->naux * nao, target);
+                     (long long)c->naux * nao, target, c->herm);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
@@ -1051,7 +1072,7 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
     P.fl_A_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[k2]].elems;
     P.fl_B_t += 8.0 * nao * nao * (double)c->part_aux[c->rep[(a * n2 + b) * n3 + cc]].elems;
   }
-  for (int w = 0; w < nw; ++w) P.fl_G_t += 8.0 * Nk * (double)c->naux * nao * c->part_ao[w].elems;
+  for (size_t b = 0; b < c->aob_n.size(); ++b) P.fl_G_t += 8.0 * Nk * (double)c->naux * nao * gram_elems(c, c->aob_n[b]);
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_B, B));
   CKS(upload(c, P.d_units, units));
@@ -1101,6 +1122,7 @@ static sgw_status self_energy_impl(sgw_ctx* c, const Z* G, const Z* Pt, const Z*
       gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(-1.0 / c->Nk), 0, st);
     });
   }
+  CKS(lower_from_upper(c, 0, out, st));
   return SGW_OK;
 }
 

@@ -251,8 +251,9 @@ struct sgw_ctx {
   cudaStream_t inv_aux[2] = {nullptr, nullptr};
   cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
-  sgw::HermItem* d_herm_items = nullptr;  // P0 blocks at every tau (lower triangles from upper)
-  int n_herm_items = 0;
+  bool herm = false;  // frequency sets closed under w -> -w: Hermitian blocks are exploited
+  sgw::HermItem* d_herm_items[2] = {nullptr, nullptr};  // Sigma~ / P0 blocks at every tau
+  int n_herm_items[2] = {0, 0};
   // iteration buffers and the captured graph
   double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
   double* h_pinned = nullptr;  // host-visible scalars written at the end of a captured iteration
@@ -320,7 +321,8 @@ inline void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
   c->prof_pending.push_back({id, a, b});
 }
 
-sgw_status p0_lower_from_upper(sgw_ctx* c, double2* P0, cudaStream_t st);
+sgw_status lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st);
+double gram_elems(const sgw_ctx* c, int nb);  // elements a Gram stage contracts in a block of nb
 
 // tensor-core chains of the chosen form (tc.cu)
 bool tc_supported(const sgw_ctx* c);

@@ -991,7 +991,7 @@ static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
       TcJob j{};
       j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
       j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit, true);
+      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit, c->herm);
       for (int t = t0; t < t1; ++t)
         gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
     }
@@ -1052,9 +1052,8 @@ static sgw_status build_p0(sgw_ctx* c) {
     T.fl_vg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     T.fl_gvg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
-  // the Gram stage needs the upper triangles of the Hermitian blocks only
-  for (size_t b = 0; b < c->auxb_n.size(); ++b)
-    T.fl_pg += 8.0 * Nk * (double)nao * nao * 0.5 * c->auxb_n[b] * (c->auxb_n[b] + 1.0);
+  // with Hermitian blocks the Gram stage needs their upper triangles only
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) T.fl_pg += 8.0 * Nk * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
   CKS(up(c, T.d_vg, vg));
   CKS(up(c, T.d_gvg, gvg));
   T.built_p0 = true;
@@ -1319,7 +1318,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
     run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
   if (tune) T.tuned_p0 = true;
-  return p0_lower_from_upper(c, out, st);
+  return lower_from_upper(c, 1, out, st);
 }
 
 sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, cudaStream_t st) {

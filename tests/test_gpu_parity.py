@@ -178,6 +178,41 @@ def test_diamond_nonsymmorphic_chain(diamond):
     assert rel_err(diamond.unf(0, diamond.lShf), diamond.Shf) < TOL
 
 
+def test_rocksalt_uses_hermitian_blocks(rocksalt):
+    """Frequency sets closed under w -> -w: the Gram stages fill the lower triangles by transposition."""
+    from paper_2405_09494_gb300 import sgw
+
+    kernels = set(sgw.sgw_profile_read(rocksalt.sess.ctx))
+    assert {"p0_mirror", "sigma_mirror"} <= kernels, kernels
+    P0u = rocksalt.unf(1, rocksalt.lP0)
+    assert np.abs(P0u - P0u.conj().transpose(0, 1, 3, 2)).max() < 1e-12 * np.abs(P0u).max()
+
+
+def test_asymmetric_frequency_sets_contract_every_tile():
+    """A bosonic and a fermionic set that are not closed under w -> -w: P(tau) and Sigma~(tau) lose
+    exact Hermiticity, so the library contracts every Gram tile; the chain still matches the oracle."""
+    _need_gpu()
+    from paper_2405_09494_gb300 import sgw
+
+    cfg = _small_rocksalt((2, 2, 2))
+    mb = sorted(cfg.mats_b)
+    mf = sorted(cfg.mats_f)
+    mb = mb[1:] + [mb[-1] + 7]  # drop the most negative bosonic index, add a positive one
+    mf = mf[1:] + [mf[-1] + 5]
+    case = Case(dataclasses.replace(cfg, name="rocksalt-asym", mats_b=mb, mats_f=mf))
+    try:
+        kernels = set(sgw.sgw_profile_read(case.sess.ctx))
+        assert not ({"p0_mirror", "sigma_mirror"} & kernels), kernels
+        assert rel_err(case.unf(1, case.lP0), case.P0) < TOL
+        assert rel_err(case.unf(1, case.lP), case.P) < TOL
+        assert rel_err(case.unf(0, case.lSig), case.Sig) < TOL
+        # the reason for the fallback: Sigma~ is no longer Hermitian beyond rounding
+        herm = np.abs(case.Sig - case.Sig.conj().transpose(0, 1, 3, 2)).max() / np.abs(case.Sig).max()
+        assert herm > 1e-9, herm
+    finally:
+        case.sess.close()
+
+
 # ------------------------------------------------------------------ one full pass (sgw_iterate)
 def test_c1_fine_full_iteration_matches_oracle(c1_fine):
     """One pass of sgw_iterate (damping, mu search) against the oracle's scgw_iteration from G0."""
