@@ -37,10 +37,15 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 
 # TF32 tensor peak from the measured bf16 burst (MEASURED_PEAKS.json) and the nominal 1.1 / 2.25 ratio;
 # the chosen form spends three TF32 products per FP32-accurate product
 TF32_X3_PEAK_TFLOPS = 1907.2 * 1.1 / 2.25 / 3
+# the same from the sustained bf16 figure, for kernels inside iterations longer than a second
+TF32_X3_SUSTAINED_TFLOPS = 1734.0 * 1.1 / 2.25 / 3
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
+HBM_PEAK_GBS = 6657.6  # measured copy bandwidth (MEASURED_PEAKS.json)
 # DRAM bytes (read + write) of one launch of a kernel class on a workload, from one ncu capture
-# (profiles/k_bd_mult_fp64_c2.md); reported as the roofline's traffic while the kernel is unchanged.
-DRAM_TRAFFIC_BYTES = {("c2", "sigma_pvg"): 4654034944 + 2777765888}
+# (profiles/k_bd_mult_fp64_c2.md, profiles/k_tc_persist_c2.md); reported as the roofline's traffic
+# while the kernel is unchanged.
+DRAM_TRAFFIC_BYTES = {("c2", "sigma_pvg"): 4654034944 + 2777765888,
+                      ("c2", "sigma_pvg_tc"): 1556365056 + 1358604800}
 
 
 def _args():
@@ -279,16 +284,48 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     return out
 
 
-def _roofline(prof, workload=None):
-    """Roofline of the kernel class with the most device time, against the peak of the pipe it runs on."""
+def _algorithmic_bytes(dom, cfg, npairs, steps):
+    """Bytes one launch of the class must move: sigma_pvg reads X1 and writes X2, each
+    npairs x ntau x naux x nao^2 complex (16 bytes in the plain form, 8 in the chosen form), per
+    step; None for the other classes."""
+    if not dom.startswith("sigma_pvg"):
+        return None
+    esize = 16 if dom == "sigma_pvg" else 8
+    return 2.0 * npairs * cfg.ntau * cfg.naux * cfg.nao * cfg.nao * esize * steps
+
+
+def _roofline(prof, workload=None, cfg=None, npairs=None, steps=1, step_s=0.0):
+    """Roofline of the kernel class with the most device time.  Its arithmetic intensity (flops per
+    algorithmic byte, where the bytes are known) against the pipe's balance point decides the bound:
+    below it the kernel is measured against the HBM copy bandwidth, above it against the peak of
+    the pipe it runs on."""
     compute = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(compute, key=lambda k: compute[k][0])
     ms, gf, nl = compute[dom]
     achieved = (gf / nl) / (ms / nl)  # GFLOP per launch / ms per launch = TFLOP/s
+    traffic = DRAM_TRAFFIC_BYTES.get((workload, dom))
     if dom.endswith("_tc"):
-        bound, peak, note = "tensor", TF32_X3_PEAK_TFLOPS, (
-            "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 burst 1907.2 TF/s "
-            "x nominal TF32/BF16 ratio 1.1/2.25 = 932 TF/s, / 3 = 311 TF/s (of measured)")
+        if step_s > 1.0:
+            bound, peak, note = "tensor", TF32_X3_SUSTAINED_TFLOPS, (
+                "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 sustained "
+                "1734 TF/s x nominal TF32/BF16 ratio 1.1/2.25 = 848 TF/s, / 3 = 283 TF/s (of measured; the "
+                "iteration lasts over a second)")
+        else:
+            bound, peak, note = "tensor", TF32_X3_PEAK_TFLOPS, (
+                "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 burst "
+                "1907.2 TF/s x nominal TF32/BF16 ratio 1.1/2.25 = 932 TF/s, / 3 = 311 TF/s (of measured)")
+        nbytes = _algorithmic_bytes(dom, cfg, npairs, steps) if cfg is not None and npairs else None
+        if nbytes:
+            ai = gf * 1e9 / nbytes
+            if ai < peak * 1e12 / (HBM_PEAK_GBS * 1e9):
+                gbs = (nbytes / nl) / (ms / nl * 1e-3) / 1e9
+                return {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                        "frac": gbs / HBM_PEAK_GBS, "traffic": traffic,
+                        "algorithmic_bytes_per_launch": nbytes / nl, "flop_per_byte": ai,
+                        "tflops": achieved, "tflops_frac_of_tensor_peak": achieved / peak,
+                        "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); the kernel's "
+                                     f"{ai:.1f} flop/byte is below the balance point of {note.split(':')[0]} "
+                                     f"({peak * 1e3 / HBM_PEAK_GBS:.1f} flop/byte)"}
     elif dom.endswith("_f32"):
         bound, peak, note = "alu", FP32_PEAK_TFLOPS, (
             "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived; a probe measured 70.4)")
@@ -296,7 +333,7 @@ def _roofline(prof, workload=None):
         bound, peak, note = "alu", FP64_PEAK_TFLOPS, (
             "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived; a DFMA probe measured 1.20)")
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": DRAM_TRAFFIC_BYTES.get((workload, dom)), "peak_note": note}
+            "frac": achieved / peak, "traffic": traffic, "peak_note": note}
 
 
 def _kernels(prof, steps):
@@ -358,13 +395,14 @@ def run_ours(args, rank, world, local):
         ref.close()
     else:
         errs = None
+    npairs = int(sess[forms[0]].layout.npairs)
     for f in forms:
         sess[f].close()
 
     def summary(f):
         r = res[f]
         gf = sum(v[1] for v in r["prof"].values()) / args.steps
-        return gf, _roofline(r["prof"], cfg.name)
+        return gf, _roofline(r["prof"], cfg.name, cfg, npairs, args.steps, r["t_step"])
 
     head = forms[0]
     gf_h, roof_h = summary(head)
