@@ -252,7 +252,9 @@ SGW_API sgw_status sgw_hartree_fock(sgw_ctx* ctx, const void* G_tau, void* Sigma
  * bracket's midpoint), starting from *mu_inout (the midpoint when outside
  * the bracket); it stops at |N - n_elec| <= 1e-11 or after 64 trials, and is
  * synchronous in that case.  *mu_inout is host: the start (or the fixed mu
- * without the search) in, the result out. */
+ * without the search) in, the result out.  A search that ends without meeting
+ * the tolerance (n_elec out of reach in [-20, 20]) returns SGW_ERR_NOCONV with
+ * *mu_inout and G_tau at its last trial. */
 SGW_API sgw_status sgw_dyson(sgw_ctx* ctx, const void* Sigma_tau, const void* Sigma_hf, double* mu_inout,
                              int search_mu, void* G_tau, sgw_stream stream);
 /* a12: total energy (Galitskii-Migdal form; the paper defines none) into
@@ -265,7 +267,8 @@ SGW_API sgw_status sgw_energy(sgw_ctx* ctx, const void* G_tau, const void* Sigma
  * (in/out), Sigma_tau, Sigma_hf (in/out; zero on the first pass) are packed;
  * *mu is host in/out: each pass's mu search (as in sgw_dyson) starts from the
  * mu of the pass before, the first from *mu.  Synchronous; fills *stats
- * (host, may be NULL). */
+ * (host, may be NULL).  A pass whose mu search does not converge stops the
+ * loop with SGW_ERR_NOCONV. */
 SGW_API sgw_status sgw_iterate(sgw_ctx* ctx, int max_iter, double damping, double tol, void* G_tau,
                                void* Sigma_tau, void* Sigma_hf, double* mu, sgw_iter_stats* stats,
                                sgw_stream stream);

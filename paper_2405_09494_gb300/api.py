@@ -30,6 +30,7 @@ class Session:
 
         self.torch = torch
         self.cfg = cfg
+        self.precision = precision
         self.device = torch.device(device)
         self.sys = system if system is not None else synth.System(cfg)
         self.ctx = sgw.sgw_create(cfg.nk, cfg.nao, cfg.naux, cfg.ntau, cfg.mats_f, cfg.mats_b, cfg.beta, cfg.n_elec,
@@ -113,6 +114,39 @@ class Session:
         sgw.sgw_unfold(self.ctx, which, nt, packed, out)
         self.torch.cuda.synchronize(self.device)
         return out
+
+    # ---- checkpoint / resume ------------------------------------------------
+    def state_key(self) -> str:
+        """Identity of the workload a saved loop state belongs to (configuration and precision)."""
+        import hashlib
+        import json
+
+        desc = {k: (list(v) if isinstance(v, tuple) else v) for k, v in vars(self.cfg).items()}
+        desc["precision"] = int(self.precision)
+        return hashlib.sha256(json.dumps(desc, sort_keys=True, default=str).encode()).hexdigest()
+
+    def save_state(self, path, G, Sig, Shf, mu, iteration=0, history=()):
+        """Write the state of the self-consistency loop to ``path`` (.npz): packed G(tau),
+        Sigma~(tau), Sigma_HF, mu and a JSON header (workload key, pass count, |Delta Sigma|
+        history).  The library keeps nothing else between passes, so this is the whole state."""
+        import json
+
+        head = dict(key=self.state_key(), iteration=int(iteration), history=[float(x) for x in history],
+                    g_elems=int(self.layout.g_elems), ntau=int(self.cfg.ntau))
+        np.savez(path, G=G.cpu().numpy(), Sig=Sig.cpu().numpy(), Shf=Shf.cpu().numpy(), mu=np.float64(mu),
+                 header=np.frombuffer(json.dumps(head).encode(), dtype=np.uint8))
+
+    def load_state(self, path):
+        """Read a state written by :meth:`save_state` for this workload: (G, Sig, Shf, mu, header)."""
+        import json
+
+        z = np.load(path)
+        head = json.loads(bytes(z["header"]).decode())
+        if head["key"] != self.state_key():
+            raise ValueError("saved loop state belongs to another workload or precision")
+        dev = self.device
+        to = lambda a: self.torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        return to(z["G"]), to(z["Sig"]), to(z["Shf"]), float(z["mu"]), head
 
     def close(self):
         if self.ctx is not None:

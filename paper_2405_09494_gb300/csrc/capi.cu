@@ -65,6 +65,11 @@ sgw_status ensure_g32(sgw_ctx* c, size_t elems) {
 }
 sgw_status ensure_workspace(sgw_ctx* c, size_t bytes) {
   if (bytes <= c->ws_bytes) return SGW_OK;
+  // fault injection on the host: SGW_FAIL_ALLOC_ABOVE_MB makes any larger workspace request fail
+  // as an allocation failure would (the context keeps its current workspace and stays usable)
+  if (const char* lim = std::getenv("SGW_FAIL_ALLOC_ABOVE_MB"))
+    if ((double)bytes > std::atof(lim) * (1 << 20))
+      return c->fail(SGW_ERR_OOM, "workspace allocation failed (injected by SGW_FAIL_ALLOC_ABOVE_MB)");
   if (c->d_ws) cudaFree(c->d_ws);
   c->d_ws = nullptr;
   c->ws_bytes = 0;
@@ -1407,10 +1412,14 @@ extern "C" SGW_API sgw_status sgw_dyson(sgw_ctx* c, const void* Sigma_tau, const
   CKS(dyson_device(c, static_cast<const double2*>(Sigma_tau), static_cast<const double2*>(Sigma_hf), *mu_inout,
                    search_mu, static_cast<double2*>(G_tau), st));
   if (search_mu) {
-    double mu = 0.0;
-    CK(cudaMemcpyAsync(&mu, c->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double sc[5] = {0, 0, 0, 0, 0};  // lo, hi, mu, done, N of the last trial
+    CK(cudaMemcpyAsync(sc, c->d_scalar, sizeof(sc), cudaMemcpyDeviceToHost, st));
     CKS(sgw_sync(c, stream));
-    *mu_inout = mu;
+    *mu_inout = sc[2];
+    if (sc[3] == 0.0)
+      return c->fail(SGW_ERR_NOCONV, "mu search: |N - n_elec| = " + std::to_string(std::fabs(sc[4] - c->p.n_elec)) +
+                                         " after 64 trials (bracket [" + std::to_string(sc[0]) + ", " +
+                                         std::to_string(sc[1]) + "]); G was built at the last mu");
   }
   return SGW_OK;
 }
@@ -1582,6 +1591,11 @@ extern "C" SGW_API sgw_status sgw_iterate(sgw_ctx* c, int max_iter, double dampi
     std::memcpy(&d2, c->h_pinned + 9, 8);
     dmax = std::max(d1, d2);
     *mu = c->h_pinned[2];
+    if (c->h_pinned[3] == 0.0) {  // the pass's mu search stopped without meeting its tolerance
+      CKS(sgw_sync(c, stream));
+      return c->fail(SGW_ERR_NOCONV, "mu search of pass " + std::to_string(it + 1) + ": |N - n_elec| = " +
+                                         std::to_string(std::fabs(c->h_pinned[4] - c->p.n_elec)) + " after 64 trials");
+    }
     if (dmax < tol) { ++it; break; }
   }
   CKS(sgw_sync(c, stream));
