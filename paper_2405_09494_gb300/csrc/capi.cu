@@ -211,9 +211,12 @@ static void schedule_units(std::vector<GramUnit>& units, size_t from, long long 
   (void)kwork;
 }
 
-// Target multiply-adds per unit so that a launch of `work` fills the GPU several times over.
+// Target multiply-adds per unit so that a launch of `work` fills the GPU several times over:
+// about 32 units per SM, i.e. six or more waves of the five resident CTAs per SM, so the last
+// wave's idle SMs cost little (at 8 units per SM the Gram stages ran two waves and the SMs were
+// busy 81% of the time).
 static long long unit_target(double work) {
-  const double t = work / (152.0 * 8.0);
+  const double t = work / (152.0 * 32.0);
   return std::max(1LL << 14, std::min(1LL << 22, (long long)t));
 }
 
