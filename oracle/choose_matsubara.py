@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE (an offline script of the oracle): it calls only
 input data, into the configuration table of the package.  Both the oracle and
 the library build their own transform matrices from those integers.
 
-Reading of the paper (Sec. 5.1 uses an IR grid, which this build replaces by a
-Chebyshev representation): the frequency set must make the map from the n
+Reading of the paper (Sec. 5.1 uses an IR grid, replaced here by a Chebyshev
+representation): the frequency set must make the map from the n
 Chebyshev-node values to the sampled Matsubara values well conditioned.  The
 set is chosen greedily by volume.  A frequency pair (nu, -nu) contributes the
 real rows Re I(nu) and Im I(nu) of the integral matrix (the complex rows of

@@ -13,8 +13,8 @@ What is computed (paper Sec. 4.1):
 * the bosonic pair of Eq. (P02P): Omega_n = 2 n pi / beta, and the inverse
   P(tau) = (1/beta) sum_n P(i Omega_n) exp(-i Omega_n tau).
 
-The paper evaluates these on an IR grid; this build uses a Chebyshev
-representation instead (reading of the paper: tau functions are represented
+The paper evaluates these on an IR grid; here a Chebyshev representation is
+used instead (reading of the paper: tau functions are represented
 by their values at the n Chebyshev roots mapped to [0, beta]; a transform is
 the exact Fourier integral of the interpolating polynomial; the inverse is the
 least-squares inverse (pseudo-inverse) of the forward map on the chosen,

@@ -14,10 +14,10 @@ Conventions (interface shared with the library through the input data only)
   array).
 * ``G, Sigma``: [Nk][ntau][nao][nao]; ``P0, P``: [Nk(q)][ntau][naux][naux];
   tau on the Chebyshev nodes of ``oracle.grid``.
-* spin-restricted closed shell, spin factor s = 2 (reading C-4 below).
+* spin-restricted closed shell, spin factor s = 2 (the spin reading below).
 
-Readings of the paper (all listed in the design doc)
------------------------------------------------
+Readings of the paper
+---------------------
 * Sign of the bare bubble: Eq. (P0) is printed with -1/N_k; combined with
   G(-tau) = -G(beta - tau) that makes P0(i Omega_0) positive semidefinite and
   the geometric series of Eq. (P02P) anti-screening.  ``loop_sign = +1`` (the
@@ -321,7 +321,8 @@ def dyson(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, n_elec=None, s=2, search_mu=
 
     Sigma~(i w) = TF Sigma~(tau); G(i w) by inversion; G(tau) = TFbar G(i w).
     With search_mu, mu solves N(mu) = N_e, N the particle number of gamma = -G(beta^-)
-    (reading C-7), by Newton's method kept inside a bracket, starting from the given mu:
+    (the module's readings of gamma and N_e), by Newton's method kept inside a bracket, starting
+    from the given mu:
       * a trial at mu gives r = N(mu) - N_e and N'(mu); stop when |r| <= n_tol;
       * the bracket [mu_lo, mu_hi] shrinks to the side of mu that keeps the root
         (N increases with mu: r > 0 moves the upper end to mu, else the lower end);
@@ -380,7 +381,7 @@ def particle_number_and_slope(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, s=2):
 
 
 def energy(H0, S, G_tau, Sigma_hf, Sigma_tau, beta, s=2):
-    """Total energy in the Galitskii-Migdal form (not defined in the paper; reading C-12).
+    """Total energy in the Galitskii-Migdal form (not defined in the paper; a reading of this module).
 
     E = (s/N_k) sum_k Tr[gamma H0] + (s/2N_k) sum_k Tr[gamma Sigma_HF] + E_c,
     E_c = -(s/2N_k) sum_k int_0^beta Tr[G^k(tau) Sigma~^k(beta - tau)] dtau.
