@@ -153,9 +153,13 @@ def chebyshev_fourier_integrals(nu: np.ndarray, beta: float, n: int, statistics:
         prev = None
         while True:
             x, wx = _gauss_legendre_panels(panels)
-            T = _cheb_T(n, x)
-            ph = np.exp(1j * a * (1.0 + x)) * wx
-            cur = 0.5 * beta * (T @ ph)
+            # the node sum in blocks of 2^15 nodes keeps the n x nodes table small at high
+            # frequencies (the same quadrature; only the order of the partial sums differs)
+            acc = np.zeros(n, dtype=np.complex128)
+            for c0 in range(0, x.size, 1 << 15):
+                xs = x[c0:c0 + (1 << 15)]
+                acc += _cheb_T(n, xs) @ (np.exp(1j * a * (1.0 + xs)) * wx[c0:c0 + (1 << 15)])
+            cur = 0.5 * beta * acc
             if prev is not None and np.max(np.abs(cur - prev)) <= tol * beta:
                 break
             prev = cur
