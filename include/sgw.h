@@ -18,8 +18,11 @@
  * are row-major.  Every tensor argument is a DEVICE pointer owned by the
  * caller unless the comment says "host".  Calls enqueue work on the given
  * CUDA stream and return; results are ready when the stream is.  The
- * library allocates its own device workspaces at set-up time and frees them
- * in sgw_destroy; caller buffers are never freed or kept after a call.
+ * library allocates its own device workspaces (on the first call that needs
+ * them, reused afterwards) and frees them in sgw_destroy; caller buffers are
+ * never freed or kept after a call.  Batched inversions may fork onto two
+ * side streams the context owns and join back to the caller's stream with
+ * events before the call's next step (also under graph capture).
  *
  * k mesh: Gamma-centred n1 x n2 x n3; point k has fractional coordinates
  * (i1/n1, i2/n2, i3/n3) in the reciprocal basis and flat index
@@ -41,9 +44,12 @@
  * Error behaviour: every call returns an sgw_status; SGW_OK means that the
  * work was enqueued (or done, for host-side calls).  Argument errors are
  * detected before anything is enqueued.  Conditions found on the device (a
- * singular pivot) are recorded in a device status word and returned by the
- * next call that synchronises (sgw_dyson with a chemical-potential search,
- * sgw_iterate, sgw_sync).  sgw_last_error gives a text for the last failure.
+ * singular or NaN pivot, a tensor-core job that fails its checks, a pipeline
+ * wait over its time limit) are recorded in a device status word and returned
+ * by the next call that synchronises (sgw_dyson with a chemical-potential
+ * search, sgw_iterate, sgw_sync), which clears it; a chemical-potential search
+ * that does not converge returns SGW_ERR_NOCONV.  sgw_last_error gives a text
+ * for the last failure.
  * A context must be used by one host thread at a time.
  */
 #ifndef SGW_H
