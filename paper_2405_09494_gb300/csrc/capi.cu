@@ -318,7 +318,8 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
-  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab); dfree(c->d_herm_items[0]); dfree(c->d_herm_items[1]);
+  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
+  for (auto& h : c->d_herm_items) dfree(h);
   for (auto& a : c->inv_aux)
     if (a) cudaStreamDestroy(a);
   for (auto& e : c->inv_ev)
@@ -699,8 +700,9 @@ extern "C" SGW_API sgw_status sgw_g0(sgw_ctx* c, double* mu_out, void* G_tau, sg
 // (Eq. (P0)) is Hermitian, and with it P^q(tau) and Sigma~^k(tau) (Eqs. (P02P), (sigma)) when
 // the frequency sets are closed under w -> -w (c->herm).  The Gram stages then contract only the
 // tiles on and above the diagonal, and this fills the strict lower triangle of every block of the
-// family (which = 0: Sigma~, orbital blocks; 1: P0, auxiliary blocks) at every tau by conjugate
-// transposition.  Without c->herm the Gram stages contract every tile and nothing is filled.
+// family (which = 0: Sigma~, orbital blocks at every tau; 1: P0, auxiliary blocks at every tau;
+// 2: Sigma_HF, orbital blocks, one matrix per wedge point) by conjugate transposition.  Without
+// c->herm the Gram stages contract every tile and nothing is filled.
 double sgw::gram_elems(const sgw_ctx* c, int nb) { return c->herm ? 0.5 * nb * (nb + 1.0) : (double)nb * nb; }
 
 sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st) {
@@ -708,18 +710,20 @@ sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t
   HermItem*& d = c->d_herm_items[which];
   int& n = c->n_herm_items[which];
   if (!d) {
-    const auto& off = which == 0 ? c->aob_off : c->auxb_off;
-    const auto& sz = which == 0 ? c->aob_n : c->auxb_n;
-    const long long elems = which == 0 ? c->g_elems : c->p_elems;
+    const auto& off = which == 1 ? c->auxb_off : c->aob_off;
+    const auto& sz = which == 1 ? c->auxb_n : c->aob_n;
+    const long long elems = which == 1 ? c->p_elems : c->g_elems;
+    const int nmat = which == 2 ? 1 : c->nt;  // Sigma_HF has no tau axis
     std::vector<HermItem> h;
-    for (int t = 0; t < c->nt; ++t)
+    for (int t = 0; t < nmat; ++t)
       for (size_t b = 0; b < off.size(); ++b)
         if (sz[b] > 1) h.push_back({(long long)t * elems + off[b], sz[b], 0});
     n = (int)h.size();
     if (h.empty()) return SGW_OK;
     CKS(upload(c, d, h));
   }
-  run(c, which == 0 ? "sigma_mirror" : "p0_mirror", 0.0, 1, st, [&] { hermitian_fill(d, n, X, st); });
+  run(c, which == 0 ? "sigma_mirror" : which == 1 ? "p0_mirror" : "hf_mirror", 0.0, 1, st,
+      [&] { hermitian_fill(d, n, X, st); });
   return SGW_OK;
 }
 
@@ -1212,7 +1216,8 @@ static sgw_status build_k_plan(sgw_ctx* c) {
       const int nb = c->aob_n[b], st = c->aob_start[b];
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, c->aob_off[b], (long long)(w - w0) * Nk * vs + (long long)st * nao,
-                     (long long)w * Nk * vs + (long long)st * nao, nao, nao, Nk, (long long)c->naux * nao, target);
+                     (long long)w * Nk * vs + (long long)st * nao, nao, nao, Nk, (long long)c->naux * nao, target,
+                     c->herm);
       finalize_units(units, from, vs, vs);
     }
     schedule_units(units, (size_t)base, 0);
@@ -1329,10 +1334,10 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
   for (size_t g = 0; g + 1 < c->plan_k_wbeg.size(); ++g) {
     const int w0 = (int)g * grp, w1 = std::min(nw, w0 + grp);
     double flz = 0, flg = 0;
-    for (int w = w0; w < w1; ++w) {
+    for (int w = w0; w < w1; ++w)
       for (int k2 = 0; k2 < Nk; ++k2) flz += 8.0 * naux * nao * (double)c->part_ao[c->rep[k2]].elems;
-      flg += 8.0 * Nk * naux * nao * (double)c->part_ao[w].elems;
-    }
+    for (size_t b = 0; b < c->aob_n.size(); ++b)
+      if (c->aob_w[b] >= w0 && c->aob_w[b] < w1) flg += 8.0 * Nk * naux * nao * gram_elems(c, c->aob_n[b]);
     run(c, "hf_k", flz, 1, st, [&] {
       bdm(c, 0, geom(1, naux * nao, nao, 0, 0, 0, 0, nao), (const double2*)c->d_V[1], Zw, (const double2*)gamma,
           c->plan_k.d_A + (size_t)w0 * Nk, (long long)(w1 - w0) * Nk, st);
@@ -1346,6 +1351,8 @@ extern "C" SGW_API sgw_status sgw_hartree_fock(sgw_ctx* c, const void* G_tau, vo
       gram_reduce(c->plan_k.d_tiles + t0, (int)(t1 - t0), part, out, z(-1.0 / Nk), 1, st);
     });
   }
+  // K (and J, Hermitian for Hermitian gamma) was added on and above the diagonal only
+  CKS(lower_from_upper(c, 2, out, st));
   CK(cudaGetLastError());
   return SGW_OK;
 }

@@ -252,8 +252,8 @@ struct sgw_ctx {
   cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
   bool herm = false;  // frequency sets closed under w -> -w: Hermitian blocks are exploited
-  sgw::HermItem* d_herm_items[2] = {nullptr, nullptr};  // Sigma~ / P0 blocks at every tau
-  int n_herm_items[2] = {0, 0};
+  sgw::HermItem* d_herm_items[3] = {nullptr, nullptr, nullptr};  // Sigma~(tau), P0(tau), Sigma_HF blocks
+  int n_herm_items[3] = {0, 0, 0};
   // iteration buffers and the captured graph
   double2 *d_it_P0 = nullptr, *d_it_P = nullptr, *d_it_S = nullptr, *d_it_H = nullptr;
   double* h_pinned = nullptr;  // host-visible scalars written at the end of a captured iteration
