@@ -5,7 +5,7 @@ index sets.  The index sets are plain input data (integers); the oracle and the
 library each build their own transform matrices from them.  They were chosen
 by the oracle's offline greedy volume search (``python -m oracle.choose_matsubara``)
 so that the Chebyshev-node -> Matsubara map is well conditioned (cond 36 at
-n_tau = 20, 140 at n_tau = 50).
+n_tau = 20, 140 at n_tau = 50, about 1.1e3 at n_tau = 200, beta = 500).
 
 Shell lists per atom (angular momenta) give the totals of the workloads:
 rocksalt / diamond cells with two atoms, nao = 2 * sum(2l+1) over the shells.
@@ -31,6 +31,8 @@ F100 = [-529, -268, -177, -132, -106, -88, -76, -67, -60, -54, -50, -46, -43, -4
 B100 = [-775, -358, -212, -150, -116, -95, -81, -70, -62, -56, -51, -47, -44, -41, -39, -37, -35, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 35, 37, 39, 41, 44, 47, 51, 56, 62, 70, 81, 95, 116, 150, 212, 358, 775]
 F150 = [-1174, -593, -392, -292, -233, -194, -166, -146, -130, -117, -107, -98, -91, -85, -80, -75, -71, -68, -65, -62, -59, -57, -55, -53, -52, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 51, 52, 54, 56, 58, 61, 64, 67, 70, 74, 79, 84, 90, 97, 106, 116, 129, 145, 165, 193, 232, 291, 391, 592, 1173]
 B150 = [-1735, -802, -474, -335, -259, -211, -179, -155, -137, -123, -111, -102, -94, -88, -82, -77, -73, -69, -66, -63, -60, -58, -56, -54, -52, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 50, 52, 54, 56, 58, 60, 63, 66, 69, 73, 77, 82, 88, 94, 102, 111, 123, 137, 155, 179, 211, 259, 335, 474, 802, 1735]
+F200 = [-2069, -1047, -691, -515, -410, -341, -292, -256, -228, -205, -187, -172, -159, -148, -138, -130, -123, -117, -111, -106, -101, -97, -93, -90, -87, -84, -81, -79, -77, -75, -73, -71, -69, -68, -66, -65, -64, -63, -62, -61, -60, -59, -58, -57, -56, -55, -54, -53, -52, -51, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64, 65, 67, 68, 70, 72, 74, 76, 78, 80, 83, 86, 89, 92, 96, 100, 105, 110, 116, 122, 129, 137, 147, 158, 171, 186, 204, 227, 255, 291, 340, 409, 514, 690, 1046, 2068]
+B200 = [-3059, -1411, -834, -590, -456, -372, -314, -272, -240, -215, -195, -179, -165, -153, -143, -134, -126, -119, -113, -108, -103, -99, -95, -91, -88, -85, -82, -79, -77, -75, -73, -71, -69, -68, -66, -65, -64, -63, -62, -61, -60, -59, -58, -57, -56, -55, -54, -53, -52, -51, -50, -49, -48, -47, -46, -45, -44, -43, -42, -41, -40, -39, -38, -37, -36, -35, -34, -33, -32, -31, -30, -29, -28, -27, -26, -25, -24, -23, -22, -21, -20, -19, -18, -17, -16, -15, -14, -13, -12, -11, -10, -9, -8, -7, -6, -5, -4, -3, -2, -1, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 46, 47, 48, 49, 50, 51, 52, 53, 54, 55, 56, 57, 58, 59, 60, 61, 62, 63, 64, 65, 66, 68, 69, 71, 73, 75, 77, 79, 82, 85, 88, 91, 95, 99, 103, 108, 113, 119, 126, 134, 143, 153, 165, 179, 195, 215, 240, 272, 314, 372, 456, 590, 834, 1411, 3059]
 
 
 @dataclass
@@ -99,7 +101,7 @@ CONFIGS = {
         description="diamond Fd-3m (non-symmorphic), 4x4x4 mesh (8 wedge points), nao 52, naux 300, 150 tau, beta 200"),
     "c5": Config(
         name="c5", index=4, structure="rocksalt", nk=(4, 4, 4), ao_shells=_shells({0: 7, 1: 6, 2: 4, 3: 1}),
-        aux_shells=_shells({0: 20, 1: 20, 2: 22, 3: 8, 4: 6}), ntau=200, beta=500.0, mats_f=[], mats_b=[],
+        aux_shells=_shells({0: 20, 1: 20, 2: 22, 3: 8, 4: 6}), ntau=200, beta=500.0, mats_f=F200, mats_b=B200,
         damping=0.5,
         description="rocksalt Oh, 4x4x4 mesh (8 wedge points), nao 104, naux 600, 200 tau, beta 500, "
                     "self-consistent loop with damping 0.5"),
