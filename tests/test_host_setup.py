@@ -120,3 +120,21 @@ def test_library_blocks_match_the_oracle_simultaneous_diagonalisation(structure)
             omegas, _, _ = sy.dirac_characters(cr, (4, 4, 4), k)
             _, sizes = sy.simultaneous_diagonalize(omegas, cr.n)
             assert sorted(sizes) == sorted(lib_blocks[w]), (structure, w, sizes, lib_blocks[w])
+
+
+def test_largest_workload_grid_is_closed_and_well_conditioned():
+    """c5 (200 tau, beta 500): both index sets are closed under w -> -w (so the Hermitian Gram
+    shortcuts apply), the library's maps are well conditioned and invert, and sampled rows of
+    the fermionic map agree with the oracle's quadrature."""
+    sgw = _lib()
+    from paper_2405_09494_gb300 import configs
+
+    cfg = configs.get("c5")
+    assert all(-n - 1 in cfg.mats_f for n in cfg.mats_f) and all(-n in cfg.mats_b for n in cfg.mats_b)
+    tau, TF, TFb, TB, TBb = sgw.sgw_host_grid(cfg.nk, cfg.nao, cfg.naux, cfg.ntau, cfg.mats_f, cfg.mats_b, cfg.beta)
+    assert np.linalg.cond(TF) < 2e3 and np.linalg.cond(TB) < 2e3
+    assert np.abs(TFb @ TF - np.eye(cfg.ntau)).max() < 1e-11
+    assert np.abs(TBb @ TB - np.eye(cfg.ntau)).max() < 1e-11
+    rows = [0, 57, 100, 199]
+    oTF = grid.forward_map([cfg.mats_f[i] for i in rows], cfg.beta, cfg.ntau, "F")
+    assert np.abs(oTF - TF[rows]).max() < 1e-12 * np.abs(TF).max()
