@@ -168,7 +168,21 @@ def oracle_sample(cfg, repeats=1):
         gw.dyson(sysm.H0, sysm.S, Shf, Sig, mu, ops, cfg.n_elec, cfg.spin, search_mu=True)
         t3 = time.perf_counter()
         times.append(Nk * (t1 - t0) + Nk * (t2 - t1) + (t3 - t2))
-    return min(times), os.cpu_count()
+    return min(times), blas_threads()
+
+
+def blas_threads() -> int:
+    """Threads the oracle's BLAS runs on: the thread-count variables numpy's BLAS reads at load
+    (the smallest one set; torchrun sets OMP_NUM_THREADS=1), else every host core."""
+    vals = []
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        try:
+            v = int(os.environ.get(var, ""))
+        except ValueError:
+            continue
+        if v > 0:
+            vals.append(v)
+    return min(vals) if vals else (os.cpu_count() or 1)
 
 
 def run_reference(args, rank, world):

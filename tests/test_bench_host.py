@@ -51,3 +51,14 @@ def test_tensor_class_above_balance_point_uses_the_sustained_peak_in_long_steps(
     assert long_step["peak"] == pytest.approx(bench.TF32_X3_SUSTAINED_TFLOPS)
     assert short_step["peak"] == pytest.approx(bench.TF32_X3_PEAK_TFLOPS)
     assert long_step["frac"] > short_step["frac"]
+
+
+def test_oracle_core_count_follows_the_blas_thread_variables(bench, monkeypatch):
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.delenv(var, raising=False)
+    assert bench.blas_threads() == (os.cpu_count() or 1)
+    monkeypatch.setenv("OMP_NUM_THREADS", "1")
+    assert bench.blas_threads() == 1
+    monkeypatch.setenv("OMP_NUM_THREADS", "6")
+    monkeypatch.setenv("OPENBLAS_NUM_THREADS", "4")
+    assert bench.blas_threads() == 4
