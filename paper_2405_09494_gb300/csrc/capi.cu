@@ -705,25 +705,44 @@ extern "C" SGW_API sgw_status sgw_g0(sgw_ctx* c, double* mu_out, void* G_tau, sg
 // c->herm the Gram stages contract every tile and nothing is filled.
 double sgw::gram_elems(const sgw_ctx* c, int nb) { return c->herm ? 0.5 * nb * (nb + 1.0) : (double)nb * nb; }
 
-sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st) {
-  if (!c->herm) return SGW_OK;
+// Block table of a family (which as in lower_from_upper), built on first use.
+static sgw_status herm_items(sgw_ctx* c, int which) {
   HermItem*& d = c->d_herm_items[which];
   int& n = c->n_herm_items[which];
-  if (!d) {
-    const auto& off = which == 1 ? c->auxb_off : c->aob_off;
-    const auto& sz = which == 1 ? c->auxb_n : c->aob_n;
-    const long long elems = which == 1 ? c->p_elems : c->g_elems;
-    const int nmat = which == 2 ? 1 : c->nt;  // Sigma_HF has no tau axis
-    std::vector<HermItem> h;
-    for (int t = 0; t < nmat; ++t)
-      for (size_t b = 0; b < off.size(); ++b)
-        if (sz[b] > 1) h.push_back({(long long)t * elems + off[b], sz[b], 0});
-    n = (int)h.size();
-    if (h.empty()) return SGW_OK;
-    CKS(upload(c, d, h));
-  }
+  if (d) return SGW_OK;
+  const auto& off = which == 1 ? c->auxb_off : c->aob_off;
+  const auto& sz = which == 1 ? c->auxb_n : c->aob_n;
+  const long long elems = which == 1 ? c->p_elems : c->g_elems;
+  const int nmat = which == 2 ? 1 : c->nt;  // Sigma_HF has no tau axis
+  std::vector<HermItem> h;
+  for (int t = 0; t < nmat; ++t)
+    for (size_t b = 0; b < off.size(); ++b) h.push_back({(long long)t * elems + off[b], sz[b], 0});
+  n = (int)h.size();
+  if (h.empty()) return SGW_OK;
+  return upload(c, d, h);
+}
+
+sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st) {
+  if (!c->herm) return SGW_OK;
+  CKS(herm_items(c, which));
+  const HermItem* d = c->d_herm_items[which];
+  const int n = c->n_herm_items[which];
   run(c, which == 0 ? "sigma_mirror" : which == 1 ? "p0_mirror" : "hf_mirror", 0.0, 1, st,
       [&] { hermitian_fill(d, n, X, st); });
+  return SGW_OK;
+}
+
+// G(tau) of Eq. (dyson) is Hermitian at every tau when H0, S, Sigma_HF and Sigma~(tau) are and the
+// fermionic set is closed under w -> -w (reading R-18): with c->herm the Dyson output is replaced
+// by its Hermitian part, which changes it only at the rounding level and keeps the loop on the
+// Hermitian subspace (an anti-Hermitian rounding component is otherwise free to grow from pass to
+// pass in an undamped loop).
+static sgw_status hermitian_g(sgw_ctx* c, double2* G, cudaStream_t st) {
+  if (!c->herm) return SGW_OK;
+  CKS(herm_items(c, 0));
+  const HermItem* d = c->d_herm_items[0];
+  const int n = c->n_herm_items[0];
+  run(c, "g_hermitian", 0.0, 1, st, [&] { hermitian_part(d, n, G, st); });
   return SGW_OK;
 }
 
@@ -1409,6 +1428,7 @@ static sgw_status dyson_device(sgw_ctx* c, const double2* Sigma_tau, const doubl
   run(c, "ft", 8.0 * nwf * (double)c->nt * ge, 1, st, [&] {
     series_map(c->d_TFbar, c->nt, nwf, Gw, ge, G_tau, ge, ge, z(1.0), 0, st);
   });
+  CKS(hermitian_g(c, G_tau, st));
   CK(cudaGetLastError());
   return SGW_OK;
 }

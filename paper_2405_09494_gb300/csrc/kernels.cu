@@ -512,12 +512,16 @@ void to_c64(const double2* a, float2* b, long long n, cudaStream_t st) {
   if (n > 0) k_to_c64<<<grid_for(n, 256, 8192), 256, 0, st>>>(a, b, n);
 }
 
-// strict lower triangle of each block from its upper triangle: one CTA per block, rows over
-// warps, columns over lanes (reads above the diagonal, writes below it: no overlap)
+// Each block made Hermitian from its upper triangle: one CTA per block, rows over warps, columns
+// over lanes (reads above the diagonal, writes below it and the diagonal's imaginary part: no
+// overlap).  A Hermitian matrix has a real diagonal; leaving the rounding-level imaginary part of
+// a diagonal computed from a slightly non-Hermitian operand would feed an anti-Hermitian
+// component back into the self-consistency loop, which can amplify it from pass to pass.
 __global__ void __launch_bounds__(256) k_hermitian_fill(const HermItem* __restrict__ items, double2* __restrict__ out) {
   const HermItem it = items[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double2* B = out + it.off;
+  for (int i = threadIdx.x; i < it.n; i += 256) B[(long long)i * it.n + i].y = 0.0;
   for (int i = warp + 1; i < it.n; i += 8)
     for (int j = lane; j < i; j += 32) {
       const double2 u = B[(long long)j * it.n + i];
@@ -526,6 +530,25 @@ __global__ void __launch_bounds__(256) k_hermitian_fill(const HermItem* __restri
 }
 void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_t st) {
   if (nitems > 0) k_hermitian_fill<<<nitems, 256, 0, st>>>(items, out);
+}
+
+// X <- (X + X^dagger) / 2 per block: one CTA per block; the thread of pair (i, j), i > j, reads
+// and writes both elements of the pair, the diagonal keeps its real part.
+__global__ void __launch_bounds__(256) k_hermitian_part(const HermItem* __restrict__ items, double2* __restrict__ X) {
+  const HermItem it = items[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double2* B = X + it.off;
+  for (int i = threadIdx.x; i < it.n; i += 256) B[(long long)i * it.n + i].y = 0.0;
+  for (int i = warp + 1; i < it.n; i += 8)
+    for (int j = lane; j < i; j += 32) {
+      const double2 lo = B[(long long)i * it.n + j], up = B[(long long)j * it.n + i];
+      const double2 m = make_double2(0.5 * (up.x + lo.x), 0.5 * (up.y - lo.y));  // (up + conj(lo)) / 2
+      B[(long long)j * it.n + i] = m;
+      B[(long long)i * it.n + j] = make_double2(m.x, -m.y);
+    }
+}
+void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t st) {
+  if (nitems > 0) k_hermitian_part<<<nitems, 256, 0, st>>>(items, X);
 }
 
 // ---------------------------------------------------------------------------

@@ -92,12 +92,15 @@ void gram_partials(const GramGeom& g, const float2* A, const float2* B, const Gr
 void gram_reduce(const GramTile* tiles, int ntiles, const float2* partial, double2* out, double2 alpha, int accumulate,
                  cudaStream_t st);
 void to_c64(const double2* a, float2* b, long long n, cudaStream_t st);
-// Hermitian blocks: out[off + i n + j] = conj(out[off + j n + i]) for i > j.
+// Hermitian blocks from their upper triangles: out[off + i n + j] = conj(out[off + j n + i]) for
+// i > j, and the imaginary part of the diagonal set to zero.
 struct HermItem {
   long long off;
   int n, pad;
 };
 void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_t st);
+// Hermitian part of every block: X <- (X + X^dagger) / 2.
+void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t st);
 
 // out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
 void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,

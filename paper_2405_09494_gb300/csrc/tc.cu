@@ -1080,7 +1080,9 @@ static sgw_status build_sigma_gram(sgw_ctx* c, long long unit) {
       TcJob j{};
       j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
       j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g, unit);
+      // Hermitian Sigma~ blocks (closed frequency sets): tiles below the diagonal are left out and
+      // the blocks' lower triangles filled by conjugate transposition after the reduction
+      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g, unit, c->herm);
       for (int t = t0; t < t1; ++t)
         for (size_t b = 0; b < c->aob_off.size(); ++b) {
           if (c->aob_w[b] != w) continue;
@@ -1178,7 +1180,8 @@ static sgw_status build_sigma(sgw_ctx* c) {
     T.fl_svg += 8.0 * naux * nao * (double)c->part_ao[c->rep[k2]].elems;
     T.fl_pvg += 8.0 * nao * nao * (double)c->part_aux[c->rep[qindex(c, k1, k2)]].elems;
   }
-  for (int w = 0; w < nw; ++w) T.fl_sg += 8.0 * Nk * (double)naux * nao * c->part_ao[w].elems;
+  // with Hermitian blocks the Gram stage needs their upper triangles only
+  for (size_t b = 0; b < c->aob_n.size(); ++b) T.fl_sg += 8.0 * Nk * (double)naux * nao * gram_elems(c, c->aob_n[b]);
   CKS(up(c, T.d_svg, svg));
   CKS(up(c, T.d_pvg, pvg));
   T.built_sigma = true;
@@ -1416,7 +1419,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
   if (tune) T.tuned_s = true;
-  return SGW_OK;
+  return lower_from_upper(c, 0, out, st);
 }
 
 }  // namespace sgw
