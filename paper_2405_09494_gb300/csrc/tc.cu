@@ -1046,6 +1046,7 @@ static sgw_status build_p0(sgw_ctx* c) {
   }
   T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size();
   T.unit_p0 = unit_override() ? unit_override() : kUnitDefault;
+  if (unit_override()) T.tuned_p0 = true;  // a fixed unit holds for the context's lifetime
   CKS(build_p0_gram(c, T.unit_p0));
   T.fl_vg = T.fl_gvg = T.fl_pg = 0;
   for (long long p = 0; p < np; ++p) {
@@ -1173,6 +1174,7 @@ static sgw_status build_sigma(sgw_ctx* c) {
   }
   T.svg_start[nt] = svg.size(); T.pvg_start[nt] = pvg.size();
   T.unit_s = unit_override() ? unit_override() : kUnitDefault;
+  if (unit_override()) T.tuned_s = true;
   CKS(build_sigma_gram(c, T.unit_s));
   T.fl_svg = T.fl_pvg = T.fl_sg = 0;
   for (long long p = 0; p < np; ++p) {
