@@ -316,61 +316,41 @@ def particle_number(gamma, S, s=2):
 
 
 def dyson(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, n_elec=None, s=2, search_mu=False,
-          mu_lo=-20.0, mu_hi=20.0, n_tol=1e-11, max_trials=64):
+          mu_lo=-20.0, mu_hi=20.0, n_tol=1e-11, max_trials=200):
     """G(tau) from Eq. (dyson), optionally with the chemical-potential search.
 
     Sigma~(i w) = TF Sigma~(tau); G(i w) by inversion; G(tau) = TFbar G(i w).
-    With search_mu, mu solves N(mu) = N_e, N the particle number of gamma = -G(beta^-)
-    (the module's readings of gamma and N_e), by Newton's method kept inside a bracket, starting
-    from the given mu:
-      * a trial at mu gives r = N(mu) - N_e and N'(mu); stop when |r| <= n_tol;
-      * the bracket [mu_lo, mu_hi] shrinks to the side of mu that keeps the root
-        (N increases with mu: r > 0 moves the upper end to mu, else the lower end);
-      * the next trial is the Newton point mu - r / N'(mu) when N' > 0, the point lies
-        strictly inside the bracket and |r| is at most half the previous trial's |r|;
-        otherwise the bracket's midpoint;
-      * after max_trials trials the next point is taken as it stands.
-    N'(mu) follows from differentiating Eq. (dyson): dG(i w)/dmu = -G(i w) S G(i w).
-    A start outside the open bracket starts at its midpoint.
+    With search_mu, mu solves N(mu) = N_e (Sec. 4.1), N the particle number of
+    gamma = -G(beta^-), by plain bisection of [mu_lo, mu_hi]: the midpoint is tried, the half
+    that keeps the root is kept (N increases with mu), until |N(mu) - N_e| <= n_tol (the given mu
+    is then not used).
     """
     TF, TFbar, nu_f = grid_ops["TF"], grid_ops["TFbar"], grid_ops["nu_f"]
     Sigma_w = to_matsubara(Sigma_tau, TF)
-    r = grid.value_at_beta_minus(TF.shape[1])
-    wgt = -(r @ TFbar)  # gamma = sum_m wgt[m] G(i w_m)
+    wgt = -(grid.value_at_beta_minus(TF.shape[1]) @ TFbar)  # gamma = sum_m wgt[m] G(i w_m)
 
     def number(mu_):
         Gw = dyson_matsubara(H0, S, Sigma_hf, Sigma_w, mu_, nu_f)
-        gam = np.einsum("m,kmij->kij", wgt, Gw)
-        dgam = -np.einsum("m,kmij,kjl,kmlp->kip", wgt, Gw, S, Gw)
-        return particle_number(gam, S, s), particle_number(dgam, S, s), Gw
+        return particle_number(np.einsum("m,kmij->kij", wgt, Gw), S, s)
 
     if search_mu:
         lo, hi = mu_lo, mu_hi
-        if not (lo < mu < hi):
-            mu = 0.5 * (lo + hi)
-        r_prev = np.inf
         for _ in range(max_trials):
-            n, dn, _ = number(mu)
-            res = n - n_elec
-            if abs(res) <= n_tol:
+            mu = 0.5 * (lo + hi)
+            n = number(mu)
+            if abs(n - n_elec) <= n_tol:
                 break
-            if res > 0:
+            if n > n_elec:
                 hi = mu
             else:
                 lo = mu
-            newton = mu - res / dn if dn > 0 else np.nan
-            if lo < newton < hi and abs(res) <= 0.5 * r_prev:
-                nxt = newton
-            else:
-                nxt = 0.5 * (lo + hi)
-            r_prev = abs(res)
-            mu = nxt
-    _, _, Gw = number(mu)
+    Gw = dyson_matsubara(H0, S, Sigma_hf, Sigma_w, mu, nu_f)
     return to_matsubara(Gw, TFbar), mu
 
 
 def particle_number_and_slope(H0, S, Sigma_hf, Sigma_tau, mu, grid_ops, s=2):
-    """(N(mu), N'(mu)) as the search of :func:`dyson` evaluates them (for pins)."""
+    """(N(mu), N'(mu)): the particle number of the Dyson solution at mu and its derivative,
+    N'(mu) from differentiating Eq. (dyson), dG(i w)/dmu = -G(i w) S G(i w)."""
     TF, TFbar, nu_f = grid_ops["TF"], grid_ops["TFbar"], grid_ops["nu_f"]
     Sigma_w = to_matsubara(Sigma_tau, TF)
     wgt = -(grid.value_at_beta_minus(TF.shape[1]) @ TFbar)

@@ -14,7 +14,13 @@ What fixes each oracle function (none of these re-types the function itself):
   that ties its index structure to the pinned P0; Hermiticity; real inputs at
   n_k = 1 give real results (Sec. 5.1).
 * hartree_fock (Eq. (sigma_hf)): the explicit four-index U = sum_Q V V route (Eq. (U_decompose)).
-* dyson / mu search / energy: reduce to the closed-form non-interacting values.
+* dyson / mu search / energy: reduce to the closed-form non-interacting values; with a static
+  Sigma_HF, to the closed form of (H0 + Sigma_HF, S); with a pole self-energy
+  Sigma~(i w) = v (i w + mu - E)^{-1} v^dagger, to the orbital block of the closed-form G of the
+  embedded quadratic system [[H0 + Sigma_HF, v], [v^dagger, E]] with overlap S + identity
+  (a Schur complement), whose particle number fixes mu and whose hybridization fixes E_c;
+  the E_hf term of the energy to the interaction energy of the determinant of gamma written
+  with the four-index U = sum_Q V V and Wick's theorem.
 
 The planted-mistake tests at the end show that plausible slips fail these pins.
 """
@@ -73,6 +79,165 @@ def test_dyson_without_self_energy_is_g0(small):
     assert abs(mu_s - small["mu"]) < 1e-8
 
 
+def _gen_eigh(A, B):
+    """Generalised eigenpairs A C = B C eps with C^dagger B C = I (scipy, independent of the oracle)."""
+    eps, C = scipy.linalg.eigh(A, B)
+    return eps, C
+
+
+def _free_fermion_tau(xi, beta, tau):
+    """g(tau) = -exp(-xi tau) / (1 + exp(-beta xi)): the transform of 1 / (i w - xi), 0 < tau < beta."""
+    return -np.exp(-xi * tau - np.logaddexp(0.0, -beta * xi))
+
+
+def _closed_form_g(Hs, Ss, mu, beta, tau):
+    """-C diag(g_{eps - mu}(tau)) C^dagger per k for the generalised problem (Hs, Ss)."""
+    out = []
+    for H, S in zip(Hs, Ss):
+        eps, C = _gen_eigh(H, S)
+        g = np.stack([_free_fermion_tau(e - mu, beta, tau) for e in eps], axis=1)  # (t, a)
+        out.append(np.einsum("ia,ta,ja->tij", C, g, C.conj()))
+    return np.stack(out)
+
+
+def _closed_form_gamma(Hs, Ss, mu, beta):
+    return np.stack([(lambda e, C: (C * _fermi(e - mu, beta)) @ C.conj().T)(*_gen_eigh(H, S)) for H, S in zip(Hs, Ss)])
+
+
+def _static_sigma(small, seed=21, scale=0.3):
+    rng = np.random.default_rng(seed)
+    Nk = small["H"].shape[0]
+    X = rng.normal(size=(Nk, 3, 3)) + 1j * rng.normal(size=(Nk, 3, 3))
+    return scale * (X + X.conj().transpose(0, 2, 1))
+
+
+def _pole_system(small, seed=31):
+    """Two poles per k: E^k = diag(e1, e2), couplings v^k (3 x 2), and the embedded (H, S)."""
+    rng = np.random.default_rng(seed)
+    H, S = small["H"], small["S"]
+    Nk = H.shape[0]
+    E = rng.uniform(-1.0, 1.0, size=(Nk, 2))
+    v = 0.3 * (rng.normal(size=(Nk, 3, 2)) + 1j * rng.normal(size=(Nk, 3, 2)))
+    Shf = _static_sigma(small)
+    Hemb = np.zeros((Nk, 5, 5), complex)
+    Semb = np.zeros((Nk, 5, 5), complex)
+    for k in range(Nk):
+        Hemb[k, :3, :3] = H[k] + Shf[k]
+        Hemb[k, :3, 3:] = v[k]
+        Hemb[k, 3:, :3] = v[k].conj().T
+        Hemb[k, 3:, 3:] = np.diag(E[k])
+        Semb[k, :3, :3] = S[k]
+        Semb[k, 3:, 3:] = np.eye(2)
+    return E, v, Shf, Hemb, Semb
+
+
+def _pole_sigma_tau(E, v, mu, beta, tau):
+    """Sigma~^k(tau) = v diag(g_{E - mu}(tau)) v^dagger."""
+    g = np.stack([[_free_fermion_tau(e - mu, beta, tau) for e in Ek] for Ek in E])  # (k, p, t)
+    return np.einsum("kip,kpt,kjp->ktij", v, g, v.conj())
+
+
+def _bisect(f, target, lo=-20.0, hi=20.0, width=1e-14):
+    while hi - lo > width:
+        mid = 0.5 * (lo + hi)
+        if f(mid) > target:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def _static_pin(small, mu=0.2):
+    """Residuals of Dyson with Sigma_HF only against G0 of (H0 + Sigma_HF, S): (G at mu, mu of the search)."""
+    H, S, ops, beta = small["H"], small["S"], small["ops"], small["beta"]
+    Nk, n = H.shape[0], small["n"]
+    Shf = _static_sigma(small)
+    zero_t = np.zeros((Nk, n, 3, 3), complex)
+    G, _ = gw.dyson(H, S, Shf, zero_t, mu, ops)
+    Gref = _closed_form_g(H + Shf, S, mu, beta, ops["tau"])
+    _, mus = gw.dyson(H, S, Shf, zero_t, 0.0, ops, n_elec=3.0, search_mu=True)
+    eps = np.concatenate([_gen_eigh(a, b)[0] for a, b in zip(H + Shf, S)])
+    muref = _bisect(lambda m: S_SPIN / Nk * _fermi(eps - m, beta).sum(), 3.0)
+    return np.abs(G - Gref).max(), abs(mus - muref)
+
+
+def _pole_pin(small, mu=0.1):
+    """Residuals of Dyson with a two-pole Sigma~ against the embedded closed form: (G at mu, mu of the search)."""
+    H, S, ops, beta = small["H"], small["S"], small["ops"], small["beta"]
+    Nk = H.shape[0]
+    E, v, Shf, Hemb, Semb = _pole_system(small)
+    G, _ = gw.dyson(H, S, Shf, _pole_sigma_tau(E, v, mu, beta, ops["tau"]), mu, ops)
+    Gref = _closed_form_g(Hemb, Semb, mu, beta, ops["tau"])[:, :, :3, :3]
+    # the search: the pole self-energy is built at the trial mu, so the root is that of the
+    # embedded system's orbital-block particle number (s/N_k) sum_k Tr[gamma_oo S]
+    def n_emb(m):
+        gam = _closed_form_gamma(Hemb, Semb, m, beta)[:, :3, :3]
+        return float(np.real(S_SPIN / Nk * np.einsum("kij,kji->", gam, S)))
+
+    muref = _bisect(n_emb, 3.0)
+    _, mus = gw.dyson(H, S, Shf, _pole_sigma_tau(E, v, muref, beta, ops["tau"]), 0.0, ops, n_elec=3.0,
+                      search_mu=True)
+    return np.abs(G - Gref).max(), abs(mus - muref)
+
+
+def test_dyson_with_static_self_energy_is_g0_of_the_shifted_hamiltonian(small):
+    rg, rmu = _static_pin(small)
+    assert rg < 1e-10 and rmu < 1e-9, (rg, rmu)
+
+
+def test_dyson_with_pole_self_energy_is_the_embedded_green_function(small):
+    rg, rmu = _pole_pin(small)
+    assert rg < 1e-10 and rmu < 1e-9, (rg, rmu)
+
+
+def _slater_interaction(gam, V, Nk):
+    """<U> in the determinant of gamma (per cell): U_{ij,kl} = sum_Q V_ij(Q) V_kl(Q) (Eq. (U_decompose)),
+    <c+_i c+_k c_l c_j> = gamma_ji gamma_lk s^2 - gamma_li gamma_jk s (Wick, spin sums), momenta conserved."""
+    U = np.einsum("abQij,cdQkl->abcdijkl", V, V)
+    e = 0.0
+    for k in range(Nk):
+        for kp in range(Nk):
+            e += S_SPIN ** 2 * np.einsum("ijkl,ji,lk->", U[k, k, kp, kp], gam[k], gam[kp])
+            e -= S_SPIN * np.einsum("ijkl,li,jk->", U[k, kp, kp, k], gam[k], gam[kp])
+    return 0.5 * e / Nk ** 2
+
+
+def _ehf_pin(fine_grid, energy=None):
+    energy = energy or gw.energy
+    beta, n, ops = fine_grid
+    nk = (1, 1, 2)
+    H, S, V = random_system(nk, 2, 3, seed=7)
+    mu = gw.mu_noninteracting(H, S, beta, 2.0)
+    G = gw.g0_tau(H, S, mu, beta, ops["tau"])
+    gam = gw.density_matrix(G)
+    Shf, _, _ = gw.hartree_fock(gam, V, nk)
+    E = energy(H, S, G, Shf, np.zeros_like(G), beta)
+    return abs(E[2] - _slater_interaction(gam, V, 2))
+
+
+def _ec_pin(small, energy=None):
+    energy = energy or gw.energy
+    H, S, ops, beta = small["H"], small["S"], small["ops"], small["beta"]
+    Nk, mu = H.shape[0], 0.1
+    E, v, Shf, Hemb, Semb = _pole_system(small)
+    G = _closed_form_g(Hemb, Semb, mu, beta, ops["tau"])[:, :, :3, :3]
+    Sig = _pole_sigma_tau(E, v, mu, beta, ops["tau"])
+    gam = _closed_form_gamma(Hemb, Semb, mu, beta)
+    # (1/beta) sum_n Tr[G Sigma~](i w_n) = Tr[G_oe v^dagger] at equal time = Tr[gamma_oe v^dagger]
+    ec_ref = S_SPIN / (2 * Nk) * np.einsum("kip,kip->", gam[:, :3, 3:], v.conj())
+    Ec = energy(H, S, G, Shf, Sig, beta)[3]
+    return abs(Ec - ec_ref), abs(ec_ref)
+
+
+def test_energy_hartree_fock_term_is_the_interaction_of_the_determinant(fine_grid):
+    assert _ehf_pin(fine_grid) < 1e-12
+
+
+def test_energy_correlation_term_is_half_the_pole_hybridization(small):
+    res, scale = _ec_pin(small)
+    assert scale > 1e-2 and res < 1e-10 * max(1.0, scale), (res, scale)
+
+
 def _interacting_sigma(small, scale=0.05, seed=5):
     """A Hermitian, tau-even self-energy pair (Sigma_HF, Sigma~(tau)) to make the Dyson step non-trivial."""
     rng = np.random.default_rng(seed)
@@ -101,7 +266,7 @@ def test_particle_number_slope_is_the_derivative(small):
 def test_mu_search_finds_the_root_from_any_start(small):
     H, S, ops = small["H"], small["S"], small["ops"]
     Shf, Sig = _interacting_sigma(small)
-    # brute force: plain bisection on N(mu) to a width of 1e-14
+    # brute force: bisection on N(mu) to a width of 1e-14 (the oracle's search stops at |N - N_e| <= 1e-11)
     lo, hi = -20.0, 20.0
     while hi - lo > 1e-14:
         mid = 0.5 * (lo + hi)
@@ -262,3 +427,44 @@ def test_planted_mistakes_fail_the_pins(small):
     fd = (gw.particle_number_and_slope(H, S, Shf, Sig, 0.1 + h, ops)[0]
           - gw.particle_number_and_slope(H, S, Shf, Sig, 0.1 - h, ops)[0]) / (2 * h)
     assert abs(slip - fd) > 1e-3 * abs(fd)
+
+
+def test_planted_dyson_and_energy_slips_fail_the_pins(small, fine_grid, monkeypatch):
+    """Slips planted into the oracle's Dyson step and energy are caught by the new pins."""
+    good = gw.dyson_matsubara
+
+    def sigma_sign(H0, S, Shf, Sw, mu, nu):  # + Sigma in place of - Sigma
+        return good(H0, S, -Shf, -Sw, mu, nu)
+
+    def mu_times_identity(H0, S, Shf, Sw, mu, nu):  # (i w + mu) S -> i w S + mu I
+        Nk, nao = H0.shape[0], H0.shape[1]
+        shift = mu * (S - np.eye(nao)[None])
+        return good(H0 + shift, S, Shf, Sw, mu, nu)
+
+    for slip in (sigma_sign, mu_times_identity):
+        monkeypatch.setattr(gw, "dyson_matsubara", slip)
+        rg_s, _ = _static_pin(small)
+        rg_p, _ = _pole_pin(small)
+        monkeypatch.setattr(gw, "dyson_matsubara", good)
+        assert max(rg_s, rg_p) > 1e-4, slip.__name__
+    # a dropped pole sign only (Sigma~ with the wrong sign, Sigma_HF right) fails the pole pin
+    monkeypatch.setattr(gw, "dyson_matsubara", lambda H0, S, Shf, Sw, mu, nu: good(H0, S, Shf, -Sw, mu, nu))
+    rg_p, _ = _pole_pin(small)
+    monkeypatch.setattr(gw, "dyson_matsubara", good)
+    assert rg_p > 1e-4
+
+    # energy: E_hf without the factor 1/2, E_c with the wrong sign, E_c without the mirror beta - tau
+    def ehf_double(H0, S, G, Shf, Sig, beta, s=2):
+        E = gw.energy(H0, S, G, Shf, Sig, beta, s)
+        return E[0] + E[2], E[1], 2 * E[2], E[3]
+
+    def ec_flipped(H0, S, G, Shf, Sig, beta, s=2):
+        E = gw.energy(H0, S, G, Shf, Sig, beta, s)
+        return E[0] - 2 * E[3], E[1], E[2], -E[3]
+
+    def ec_no_mirror(H0, S, G, Shf, Sig, beta, s=2):
+        return gw.energy(H0, S, G, Shf, Sig[:, ::-1], beta, s)
+
+    assert _ehf_pin(fine_grid, ehf_double) > 1e-3
+    assert _ec_pin(small, ec_flipped)[0] > 1e-3
+    assert _ec_pin(small, ec_no_mirror)[0] > 1e-4
