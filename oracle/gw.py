@@ -175,7 +175,7 @@ def g_minus_tau(G):
 # --------------------------------------------------------------------------
 # P0, P, Sigma
 # --------------------------------------------------------------------------
-def polarization(G, V, nk, s=2, loop_sign=+1, qs=None, pairs=None):
+def polarization(G, V, nk, s=2, loop_sign=+1, qs=None, pairs=None, taus=None):
     """Bare bubble P0^q_{QQ'}(tau) of Eq. (P0) for every q of the mesh.
 
     P0^q_{QQ'}(tau) = loop_sign (s/N_k) sum_k sum_{abcd}
@@ -186,13 +186,16 @@ def polarization(G, V, nk, s=2, loop_sign=+1, qs=None, pairs=None):
         P0_{QQ'}   += sum_{ca} X1(Q)_{ca} X2(Q')_{ac}.
     ``qs`` restricts the evaluation to a list of q (other entries stay zero); ``pairs``, a set
     of (k, k + q), to the terms of those pairs (a partial sum over k, as one rank of a partition
-    of the pairs computes it).
+    of the pairs computes it); ``taus``, to a list of tau indices (G is still needed at every
+    tau: G(-tau_j) is read at the mirror node).
     """
     Vf = as_vfun(V)
-    Nk, nt, nao, _ = G.shape
+    Nk, ntau, nao, _ = G.shape
+    ts = np.arange(ntau) if taus is None else np.asarray(taus)
+    nt = ts.size
     Gm = g_minus_tau(G)
     naux = Vf(0, 0).shape[0]
-    P0 = np.zeros((Nk, nt, naux, naux), dtype=np.complex128)
+    P0 = np.zeros((Nk, ntau, naux, naux), dtype=np.complex128)
     for q in (range(Nk) if qs is None else qs):
         for k in range(Nk):
             kq = kadd(nk, k, q)
@@ -201,15 +204,15 @@ def polarization(G, V, nk, s=2, loop_sign=+1, qs=None, pairs=None):
             Vkq = Vf(k, kq)  # [Q][d][a]
             Vqk = Vf(kq, k)  # [Q'][b][c]
             # X1[t][c][Q][a] = sum_d G^k(-tau)[t][c][d] V^{k,k+q}[Q][d][a]   (one GEMM over all t, Q)
-            X1 = (Gm[k].reshape(nt * nao, nao) @ Vkq.transpose(1, 0, 2).reshape(nao, naux * nao))
+            X1 = (Gm[k][ts].reshape(nt * nao, nao) @ Vkq.transpose(1, 0, 2).reshape(nao, naux * nao))
             X1 = X1.reshape(nt, nao, naux, nao)
             # X2[t][a][Q'][c] = sum_b G^{k+q}(tau)[t][a][b] V^{k+q,k}[Q'][b][c]
-            X2 = (G[kq].reshape(nt * nao, nao) @ Vqk.transpose(1, 0, 2).reshape(nao, naux * nao))
+            X2 = (G[kq][ts].reshape(nt * nao, nao) @ Vqk.transpose(1, 0, 2).reshape(nao, naux * nao))
             X2 = X2.reshape(nt, nao, naux, nao)
             # P0[t][Q][Q'] += sum_{c,a} X1[t][c][Q][a] X2[t][a][Q'][c]
             A = X1.transpose(0, 2, 1, 3).reshape(nt, naux, nao * nao)  # [t][Q][(c,a)]
             B = X2.transpose(0, 2, 3, 1).reshape(nt, naux, nao * nao)  # [t][Q'][(c,a)]
-            P0[q] += np.matmul(A, B.transpose(0, 2, 1))
+            P0[q, ts] += np.matmul(A, B.transpose(0, 2, 1))
     P0 *= loop_sign * s / Nk
     return P0
 
@@ -232,7 +235,7 @@ def screened_interaction(P0_tau, TB, TBbar):
     return to_matsubara(Pw, TBbar), P0w, Pw
 
 
-def self_energy(G, P, V, nk, ks=None, pairs=None):
+def self_energy(G, P, V, nk, ks=None, pairs=None, taus=None):
     """Dynamic GW self-energy of Eq. (sigma) for every k of the mesh.
 
     Sigma^k_ij(tau) = -(1/N_k) sum_q sum_ab sum_QQ'
@@ -242,10 +245,13 @@ def self_energy(G, P, V, nk, ks=None, pairs=None):
         X2(Q')_{ib} = sum_Q X1(Q)_{ib} P^q_{QQ'}(tau),
         Sigma_ij   += sum_{Q' b} X2(Q')_{ib} V^{k-q,k}_{bj}(Q').
     ``ks`` restricts the evaluation to a list of k (other entries stay zero); ``pairs``, a set
-    of (k, k - q), to the terms of those pairs (a partial sum over q).
+    of (k, k - q), to the terms of those pairs (a partial sum over q); ``taus``, to a list of tau
+    indices (G and P are read at those only).
     """
     Vf = as_vfun(V)
-    Nk, nt, nao, _ = G.shape
+    Nk, ntau, nao, _ = G.shape
+    ts = np.arange(ntau) if taus is None else np.asarray(taus)
+    nt = ts.size
     naux = P.shape[-1]
     Sig = np.zeros_like(G)
     for k in (range(Nk) if ks is None else ks):
@@ -256,13 +262,13 @@ def self_energy(G, P, V, nk, ks=None, pairs=None):
             V1 = Vf(k, kmq)  # [Q][i][a]
             V2 = Vf(kmq, k)  # [Q'][b][j]
             # X1[Q][i][t][b] = sum_a V^{k,k-q}[Q][i][a] G^{k-q}(tau)[t][a][b]   (one GEMM over all Q, t)
-            X1 = V1.reshape(naux * nao, nao) @ G[kmq].transpose(1, 0, 2).reshape(nao, nt * nao)
+            X1 = V1.reshape(naux * nao, nao) @ G[kmq][ts].transpose(1, 0, 2).reshape(nao, nt * nao)
             X1 = X1.reshape(naux, nao, nt, nao).transpose(2, 0, 1, 3).reshape(nt, naux, nao * nao)
             # X2[t][Q'][(i,b)] = sum_Q P^q(tau)[t][Q][Q'] X1[t][Q][(i,b)]
-            X2 = np.matmul(P[q].transpose(0, 2, 1), X1)
+            X2 = np.matmul(P[q][ts].transpose(0, 2, 1), X1)
             # Sigma[t][i][j] += sum_{Q',b} X2[t][Q'][i][b] V^{k-q,k}[Q'][b][j]
             X2 = X2.reshape(nt, naux, nao, nao).transpose(0, 2, 1, 3).reshape(nt, nao, naux * nao)
-            Sig[k] += np.matmul(X2, V2.reshape(naux * nao, nao))
+            Sig[k, ts] += np.matmul(X2, V2.reshape(naux * nao, nao))
     Sig *= -1.0 / Nk
     return Sig
 

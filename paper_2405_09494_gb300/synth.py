@@ -366,7 +366,8 @@ class System:
             return self._vcache[p]
         cfg = self.cfg
         rng = _rng(cfg, 2, p[0], p[1])
-        X = _cgauss(rng, (self.naux, self.nao, self.nao)) / np.sqrt(self.naux)
+        # optional coupling scale of the workload (cfg.extra["vscale"], default 1)
+        X = _cgauss(rng, (self.naux, self.nao, self.nao)) * (cfg.extra.get("vscale", 1.0) / np.sqrt(self.naux))
         if self.device is not None:
             import torch
 
