@@ -77,7 +77,7 @@ typedef enum {
   SGW_ERR_OOM = 3,           /* device allocation failed                                   */
   SGW_ERR_SINGULAR = 4,      /* zero pivot in a W solve or Dyson inversion                 */
   SGW_ERR_NOCONV = 5,        /* chemical-potential bisection did not bracket / converge    */
-  SGW_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait ran out                    */
+  SGW_ERR_TIMEOUT = 6,       /* a bounded device wait ran out (sgw_set_wait_limit)         */
   SGW_ERR_UNIMPLEMENTED = 7, /* feature not built                                          */
   SGW_ERR_STATE = 8          /* call out of order (e.g. before sgw_build_irrep_basis)       */
 } sgw_status;
@@ -303,6 +303,16 @@ SGW_API sgw_status sgw_host_symmetry(const sgw_params* params, const sgw_structu
                                      int* ao_blocks, int* aux_blocks);
 
 /* ---- instrumentation (not part of the method) ---------------------------- */
+
+/* Time limit (ns) of each wait inside the chosen form's tensor-core pipeline
+ * kernel (a stage of copies landing, a stage split, an accumulator filled or
+ * drained), applied from the next launch on; 2 s when the context is created.
+ * A wait over the limit stops the kernel's CTA cleanly (its copies in flight
+ * are waited for, its tensor memory freed) and records SGW_ERR_TIMEOUT, which
+ * the next synchronising call returns; results of that call are then invalid,
+ * the context stays usable.  0 gives up at the first wait that is not
+ * already satisfied (for tests of this path).  Not part of the method. */
+SGW_API sgw_status sgw_set_wait_limit(sgw_ctx* ctx, unsigned long long ns);
 
 /* Turn per-kernel CUDA-event timing on (1) or off (0).  Events are recorded on
  * the stream each kernel is launched on.  Launch counts and algorithmic flop

@@ -1723,6 +1723,12 @@ static double trials_done(sgw_ctx* c) {
   return v;
 }
 
+extern "C" SGW_API sgw_status sgw_set_wait_limit(sgw_ctx* c, unsigned long long ns) {
+  if (!c) return SGW_ERR_ARG;
+  c->tc_wait_ns = ns;
+  return SGW_OK;
+}
+
 extern "C" SGW_API sgw_status sgw_profile_enable(sgw_ctx* c, int on) {
   if (!c) return SGW_ERR_ARG;
   if (on && !c->prof_on) c->prof_trials_seen = trials_done(c);

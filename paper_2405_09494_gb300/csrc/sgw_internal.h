@@ -273,6 +273,7 @@ struct sgw_ctx {
   double2* d_ws = nullptr;
   size_t ws_bytes = 0;
   int* d_status = nullptr;
+  unsigned long long tc_wait_ns = 2000000000ULL;  // limit of each wait in the tensor-core pipeline kernel
   double* d_scalar = nullptr;  // small host-visible results
   double dy_trial_flops = 0.0; // algorithmic flops of one mu-search trial (set by Dyson)
   double prof_trials_seen = 0.0; // trial count (d_scalar[16]) when profiling was last switched on / read

@@ -64,6 +64,7 @@ struct TcArgs {
   long long Rs, S1, S2;  // affine store: out[out_off + (R / Rs) S1 + (R % Rs) + n S2], R = tile row
   float2 alpha;
   float2* out;
+  unsigned long long wait_ns;  // limit of each pipeline wait (SGW_ERR_TIMEOUT beyond it)
 };
 
 // Cached jobs of the tensor-core chains.
@@ -97,7 +98,9 @@ namespace {
 
 constexpr int kTileBytes = 128 * 64;         // 128 rows x 16 fp32 (one swizzle row each)
 constexpr int kStageBytes = 6 * kTileBytes;  // A head, A tail, B1 head, B1 tail, B2 head, B2 tail
-constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s
+// Drain waits (copies in flight, MMAs issued) always allow 2 s: a CTA must not exit while a copy
+// into its shared memory can still land.  The pipeline waits use the context's limit (TcArgs).
+constexpr unsigned long long kDrainNs = 2000000000ULL;
 constexpr int kSlotD = 128 * 64;             // same, drained kernels (N <= 64)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -124,15 +127,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of the given parity; false after kWaitNs (sets *abort) or once *abort is set
-// by another role (if honour_abort).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, bool honour_abort = true) {
+// Wait for the phase of the given parity; false once limit_ns have passed since the first failed
+// try (sets *abort; a limit of 0 gives up at the first failed try) or once *abort is set by another
+// role (if honour_abort).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, unsigned long long limit_ns,
+                          bool honour_abort = true) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (honour_abort && *abort) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 >= limit_ns) {
       *abort = 1;
       return false;
     }
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
           const int s = (int)(gk % kPStages);
           const long long round = gk / kPStages;
-          if (round > 0 && !mbar_wait(su32(&bar_empty[s]), (uint32_t)((round - 1) & 1), &abort_flag)) {
+          if (round > 0 && !mbar_wait(su32(&bar_empty[s]), (uint32_t)((round - 1) & 1), &abort_flag, args.wait_ns)) {
             ok = false;
             break;
           }
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       // copies still in flight must land before the CTA exits: the last chunk issued on stage s
       // is the largest g < gk with g = s (mod stages)
       for (int s = 0; s < kPStages; ++s)
-        if (gk > s) mbar_wait(su32(&bar_full[s]), (uint32_t)(((gk - 1 - s) / kPStages) & 1), &abort_flag, false);
+        if (gk > s) mbar_wait(su32(&bar_full[s]), (uint32_t)(((gk - 1 - s) / kPStages) & 1), &abort_flag, kDrainNs, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
           if (kk % per == 0) {
             const int b = (int)(gi % NB);
-            if (gi >= NB && !mbar_wait(su32(&bar_acce[b]), (uint32_t)(((gi / NB) - 1) & 1), &abort_flag)) {
+            if (gi >= NB && !mbar_wait(su32(&bar_acce[b]), (uint32_t)(((gi / NB) - 1) & 1), &abort_flag, args.wait_ns)) {
               ok = false;
               break;
             }
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
           const int s = (int)(gk % kPStages);
           const long long round = gk / kPStages;
-          if (!mbar_wait(su32(&bar_ready[s]), (uint32_t)(round & 1), &abort_flag)) {
+          if (!mbar_wait(su32(&bar_ready[s]), (uint32_t)(round & 1), &abort_flag, args.wait_ns)) {
             ok = false;
             break;
           }
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       }
       // every MMA issued so far has completed once bar_done fires
       umma_commit(su32(&bar_done));
-      mbar_wait(su32(&bar_done), 0, &abort_flag, false);
+      mbar_wait(su32(&bar_done), 0, &abort_flag, kDrainNs, false);
     }
   } else if (warp >= 4 && warp < 8) {
     // ---- splitter
@@ -417,7 +422,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
       for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
         const int s = (int)(gk % kPStages);
         const long long round = gk / kPStages;
-        if (!mbar_wait(su32(&bar_full[s]), (uint32_t)(round & 1), &abort_flag)) {
+        // the outcome of the wait is made warp-uniform before the warp's .sync.aligned tensor-memory
+        // stores: lanes that saw the phase complete must not run them without the lanes that gave up
+        if (!__all_sync(0xffffffffu, mbar_wait(su32(&bar_full[s]), (uint32_t)(round & 1), &abort_flag, args.wait_ns))) {
           ok = false;
           break;
         }
@@ -506,7 +513,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
       };
       for (int it = 0; it < n_int; ++it, ++gi) {
         const int b = (int)(gi % NB);
-        if (!mbar_wait(su32(&bar_accf[b]), (uint32_t)((gi / NB) & 1), &abort_flag)) {
+        // warp-uniform outcome before the .sync.aligned tensor-memory loads (as in the splitter)
+        if (!__all_sync(0xffffffffu, mbar_wait(su32(&bar_accf[b]), (uint32_t)((gi / NB) & 1), &abort_flag, args.wait_ns))) {
           ok = false;
           break;
         }
@@ -754,8 +762,10 @@ sgw_status launch_gemm(sgw_ctx* c, const CUtensorMap& am, const CUtensorMap& bm,
   }
   const long long nunits = njobs * a.mtiles;
   const unsigned grid = (unsigned)std::min<long long>(nunits, g_sms[dev]);
+  TcArgs args = a;
+  args.wait_ns = c->tc_wait_ns;
   // one CTA per SM (the stage ring fills most of shared memory; all 512 tensor-memory columns)
-  k_tc_persist<CONJ, DRAIN><<<grid, kPThreads, kPSmem, st>>>(am, bm, jobs, a, nunits, c->d_status);
+  k_tc_persist<CONJ, DRAIN><<<grid, kPThreads, kPSmem, st>>>(am, bm, jobs, args, nunits, c->d_status);
   return SGW_OK;
 }
 

@@ -26,7 +26,7 @@ EXPORTS = [
     "sgw_get_wedge", "sgw_get_blocks", "sgw_get_pairs", "sgw_get_basis", "sgw_load_one_body", "sgw_load_v",
     "sgw_g0", "sgw_polarization", "sgw_screened_interaction", "sgw_self_energy", "sgw_hartree_fock", "sgw_dyson",
     "sgw_energy", "sgw_iterate", "sgw_unfold", "sgw_host_grid", "sgw_host_symmetry", "sgw_profile_enable",
-    "sgw_profile_read", "sgw_screened_interaction_noalloc",
+    "sgw_profile_read", "sgw_screened_interaction_noalloc", "sgw_set_wait_limit",
 ]
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "sgw_host_symmetry": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp, vp], i),
         "sgw_screened_interaction_noalloc": ([vp, vp, vp, vp], i),
         "sgw_profile_enable": ([vp, i], i),
+        "sgw_set_wait_limit": ([vp, ctypes.c_ulonglong], i),
         "sgw_profile_read": ([vp, i, ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(d),
                               ctypes.POINTER(ll), ctypes.POINTER(i), i], i),
     }
@@ -298,6 +299,11 @@ def sgw_iterate(ctx, max_iter, damping, tol, G_tau, Sigma_tau, Sigma_hf, mu, str
 
 def sgw_unfold(ctx, which, nt, packed, ao_full, stream=None):
     _check(load_library().sgw_unfold(ctx, which, nt, _ptr(packed), _ptr(ao_full), _stream(stream)), ctx)
+
+
+def sgw_set_wait_limit(ctx, ns):
+    """Limit (ns) of each wait in the tensor-core pipeline kernel (2 s at creation; see sgw.h)."""
+    _check(load_library().sgw_set_wait_limit(ctx, int(ns)), ctx)
 
 
 def sgw_profile_enable(ctx, on=True):

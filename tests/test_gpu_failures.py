@@ -7,6 +7,10 @@
 * An allocation failure injected through SGW_FAIL_ALLOC_ABOVE_MB returns SGW_ERR_OOM; the same
   call succeeds once the injection is lifted.
 * Resuming the loop from a saved state reproduces an uninterrupted run bit for bit (plain form).
+* A bounded wait of the tensor-core pipeline kernel that runs out: with the wait limit set to 0
+  the first wait that is not already satisfied gives up (no copy is broken: the copies land, the
+  kernel just stops waiting for them); the call then reports SGW_ERR_TIMEOUT at the next
+  synchronisation, and the same context computes normally once the limit is restored.
 """
 import dataclasses
 import os
@@ -147,3 +151,28 @@ def test_resume_from_saved_state_is_bitwise(tmp_path):
         other.load_state(path)
     for s in (s1, s3, other):
         s.close()
+
+
+def test_pipeline_wait_over_its_limit_is_timeout_and_context_recovers():
+    torch = _need_gpu()
+    from paper_2405_09494_gb300 import api, configs, sgw
+
+    cfg = configs.get("t1")
+    sess = api.Session(cfg, precision=sgw.SGW_MIXED_FP32)
+    try:
+        G, mu = sess.g0()
+        ref = sess.polarization(G)  # default limit: a normal call
+        sgw.sgw_sync(sess.ctx)
+        sgw.sgw_set_wait_limit(sess.ctx, 0)
+        sess.polarization(G)
+        with pytest.raises(sgw.SGWError) as e:
+            sgw.sgw_sync(sess.ctx)
+        assert e.value.status == 6, e.value  # SGW_ERR_TIMEOUT
+        sgw.sgw_sync(sess.ctx)  # the status word was cleared by the report
+        sgw.sgw_set_wait_limit(sess.ctx, 2_000_000_000)
+        again = sess.polarization(G)
+        sgw.sgw_sync(sess.ctx)
+        torch.cuda.synchronize()
+        assert torch.equal(again, ref)
+    finally:
+        sess.close()
