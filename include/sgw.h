@@ -223,6 +223,19 @@ SGW_API sgw_status sgw_g0(sgw_ctx* ctx, double* mu_out, void* G_tau, sgw_stream 
  * triangle is written as the conjugate transpose of the upper one (here and in
  * sgw_self_energy); otherwise every tile is contracted. */
 SGW_API sgw_status sgw_polarization(sgw_ctx* ctx, const void* G_tau, void* P0_tau, sgw_stream stream);
+/* a3 restricted to the momentum pairs [pair_begin, pair_end) of the
+ * polarization pair list (orientation 0 of sgw_get_pairs, ordered
+ * p = w N_k + k for the pair (k, k + q_w)): the partial sum of Eq. (P0) over
+ * those pairs, with the same normalisation (s / N_k).  The sum of the partial
+ * results of ranges that cover the list once equals sgw_polarization (the
+ * pair units of Algorithm 3 are independent, Sec. 5.2): one rank per range,
+ * then one sum over the ranks.  Every block of P0_tau is written (blocks of
+ * wedge points with no pair in the range are zero).  0 <= pair_begin <=
+ * pair_end <= nwedge N_k, else SGW_ERR_ARG; an empty range gives zeros.  The
+ * context keeps the plan of the last partial range asked for (and that of
+ * the whole list); asking for another range rebuilds it. */
+SGW_API sgw_status sgw_polarization_pairs(sgw_ctx* ctx, const void* G_tau, void* P0_tau, long long pair_begin,
+                                          long long pair_end, sgw_stream stream);
 /* a4 + a5 + a6: P0(tau) -> P0(i Omega) -> P = [I - P0]^{-1} P0 per block
  * (Eq. (P02P), FP64 in both forms) -> P(tau). */
 SGW_API sgw_status sgw_screened_interaction(sgw_ctx* ctx, const void* P0_tau, void* P_tau, sgw_stream stream);
@@ -230,6 +243,14 @@ SGW_API sgw_status sgw_screened_interaction(sgw_ctx* ctx, const void* P0_tau, vo
  * orbital blocks only.  Sigma_tau packed [ntau][g_elems]. */
 SGW_API sgw_status sgw_self_energy(sgw_ctx* ctx, const void* G_tau, const void* P_tau, void* Sigma_tau,
                                    sgw_stream stream);
+/* a7 restricted to the momentum pairs [pair_begin, pair_end) of the
+ * self-energy pair list (orientation 1, p = w N_k + k2 for the pair (k_w, k2)):
+ * the partial sum of Eq. (sigma) over those pairs (Algorithm 4's pair units),
+ * normalisation -1/N_k; the partial results of ranges that cover the list once
+ * add up to sgw_self_energy.  Ranges, zero blocks and errors as in
+ * sgw_polarization_pairs. */
+SGW_API sgw_status sgw_self_energy_pairs(sgw_ctx* ctx, const void* G_tau, const void* P_tau, void* Sigma_tau,
+                                         long long pair_begin, long long pair_end, sgw_stream stream);
 /* The paper has no counterpart to this entry point: it is sgw_screened_interaction for
  * callers that may not allocate device memory when they call (code running while a CUDA graph
  * is being captured, where cudaMalloc is not permitted, or applications that fix their device

@@ -79,9 +79,13 @@ class Session:
         mu = sgw.sgw_g0(self.ctx, G)
         return G, mu
 
-    def polarization(self, G):
+    def polarization(self, G, pairs=None):
+        """P0(tau); with ``pairs`` = (begin, end), the partial sum over that range of the pair list."""
         P0 = self.p_series()
-        sgw.sgw_polarization(self.ctx, G, P0)
+        if pairs is None:
+            sgw.sgw_polarization(self.ctx, G, P0)
+        else:
+            sgw.sgw_polarization_pairs(self.ctx, G, P0, pairs[0], pairs[1])
         return P0
 
     def screened(self, P0):
@@ -89,9 +93,13 @@ class Session:
         sgw.sgw_screened_interaction(self.ctx, P0, P)
         return P
 
-    def self_energy(self, G, P):
+    def self_energy(self, G, P, pairs=None):
+        """Sigma~(tau); with ``pairs`` = (begin, end), the partial sum over that range of the pair list."""
         Sig = self.g_series()
-        sgw.sgw_self_energy(self.ctx, G, P, Sig)
+        if pairs is None:
+            sgw.sgw_self_energy(self.ctx, G, P, Sig)
+        else:
+            sgw.sgw_self_energy_pairs(self.ctx, G, P, Sig, pairs[0], pairs[1])
         return Sig
 
     def hartree_fock(self, G):

@@ -317,6 +317,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   dfree(c->d_el_boff); dfree(c->d_el_eoff); dfree(c->d_el_bn); dfree(c->d_el_i); dfree(c->d_el_j); dfree(c->d_el_w);
   dfree(c->d_C0); dfree(c->d_eps0); dfree(c->d_epsw);
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
+  free_plan(c->plan_p0_part); free_plan(c->plan_sigma_part);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
   dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
   for (auto& h : c->d_herm_items) dfree(h);
@@ -465,6 +466,7 @@ extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_struct
       cudaMalloc(&c->d_S, c->g_elems * sizeof(double2)) != cudaSuccess)
     return c->fail(SGW_ERR_OOM, "allocating one-body blocks");
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
+  free_plan(c->plan_p0_part); free_plan(c->plan_sigma_part);
   tc_free(c);
   c->use_tc = tc_supported(c);
   c->built = true;
@@ -746,11 +748,15 @@ static sgw_status hermitian_g(sgw_ctx* c, double2* G, cudaStream_t st) {
   return SGW_OK;
 }
 
-static sgw_status build_p0_plan(sgw_ctx* c) {
-  ContractionPlan& P = c->plan_p0;
-  if (P.built) return SGW_OK;
-  const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao;
-  const long long vs = vsize(c), np = (long long)nw * Nk;
+// Plans of the block-multiply / Gram chains cover the pairs [pb, pe) of their orientation's pair
+// list (ordered [wedge point][k]); the intermediates are indexed by the local pair p - pb.
+static sgw_status build_p0_plan(sgw_ctx* c, ContractionPlan& P, long long pb, long long pe) {
+  if (P.built && P.pb == pb && P.pe == pe) return SGW_OK;
+  free_plan(P);
+  P.pb = pb;
+  P.pe = pe;
+  const int Nk = c->Nk, nt = c->nt, nao = c->nao;
+  const long long vs = vsize(c), np = pe - pb;
   const size_t budget = workspace_budget();
   int nc = (int)std::max<long long>(1, (long long)(budget * 0.8 / (2.0 * np * vs * sizeof(double2))));
   nc = std::min(nc, nt);
@@ -759,9 +765,10 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
   std::vector<BdItem> A((size_t)nt * np), B((size_t)nt * np);
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
-    for (long long p = 0; p < np; ++p) {
+    for (long long lp = 0; lp < np; ++lp) {
+      const long long p = pb + lp;
       const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
-      const long long pos = (p * nc + tl) * vs;
+      const long long pos = (lp * nc + tl) * vs;
       BdItem a;
       a.x_off = p * vs;
       a.y_off = pos;
@@ -769,7 +776,7 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
       a.part = c->rep[k2];
       a.pad = 0;
       a.scale = z(1.0);
-      A[(size_t)t * np + p] = a;
+      A[(size_t)t * np + lp] = a;
       BdItem b;
       b.x_off = pos;
       b.y_off = pos;
@@ -777,7 +784,7 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
       b.part = c->rep[k1];
       b.pad = 0;
       b.scale = z(-1.0);  // G(-tau_j) = -G(tau_{n-1-j})
-      B[(size_t)t * np + p] = b;
+      B[(size_t)t * np + lp] = b;
     }
   }
   std::vector<GramUnit> units;
@@ -798,11 +805,14 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
     const int tl = t % nc;
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
       const int w = c->auxb_w[b], nb = c->auxb_n[b], st = c->auxb_start[b];
-      const long long p0 = (long long)w * Nk;
+      // the pairs of wedge point w inside the range (none: the block stays zero)
+      const long long p0 = std::max(pb, (long long)w * Nk), p1 = std::min(pe, (long long)(w + 1) * Nk);
+      if (p1 <= p0) continue;
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->p_elems + c->auxb_off[b],
-                     (p0 * nc + tl) * vs + (long long)st * nao * nao, p0 * vs + (long long)st * nao * nao,
-                     (long long)nao * nao, (long long)nao * nao, Nk, (long long)nao * nao, target, c->herm);
+                     ((p0 - pb) * nc + tl) * vs + (long long)st * nao * nao, p0 * vs + (long long)st * nao * nao,
+                     (long long)nao * nao, (long long)nao * nao, (int)(p1 - p0), (long long)nao * nao, target,
+                     c->herm);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
@@ -815,13 +825,16 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
     P.max_units_chunk = std::max(P.max_units_chunk, P.unit_start[t1] - P.unit_start[t0]);
   }
   P.fl_A_t = P.fl_B_t = P.fl_G_t = 0;
-  for (long long p = 0; p < np; ++p) {
+  for (long long p = pb; p < pe; ++p) {
     P.fl_A_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     P.fl_B_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
   // with Hermitian blocks the Gram stage needs their upper triangles only
-  for (size_t b = 0; b < c->auxb_n.size(); ++b)
-    P.fl_G_t += 8.0 * Nk * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) {
+    const int w = c->auxb_w[b];
+    const long long npw = std::max(0LL, std::min(pe, (long long)(w + 1) * Nk) - std::max(pb, (long long)w * Nk));
+    P.fl_G_t += 8.0 * npw * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
+  }
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_B, B));
   CKS(upload(c, P.d_units, units));
@@ -831,8 +844,8 @@ static sgw_status build_p0_plan(sgw_ctx* c) {
 }
 
 template <typename Z>
-static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2* out, cudaStream_t st, const char* tag) {
-  ContractionPlan& P = c->plan_p0;
+static sgw_status polarization_impl(sgw_ctx* c, const ContractionPlan& P, const Z* G, const Z* V, double2* out,
+                                    cudaStream_t st, const char* tag) {
   const int nt = c->nt, nao = c->nao, naux = c->naux, nc = P.nc;
   const long long vs = vsize(c), np = P.items_per_t;
   const size_t inter = (size_t)np * nc * vs;
@@ -874,26 +887,44 @@ static sgw_status polarization_impl(sgw_ctx* c, const Z* G, const Z* V, double2*
   return SGW_OK;
 }
 
-extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, void* P0_tau, sgw_stream stream) {
+static sgw_status polarization_range(sgw_ctx* c, const void* G_tau, void* P0_tau, long long pb, long long pe,
+                                     sgw_stream stream) {
   CKS(need_built(c));
   if (!c->have_v[0]) return c->fail(SGW_ERR_STATE, "polarization pairs of V not loaded");
-  if (!G_tau || !P0_tau) return SGW_ERR_ARG;
-  if (!c->use_tc) CKS(build_p0_plan(c));
+  const long long np = (long long)c->nwedge * c->Nk;
+  if (!G_tau || !P0_tau || pb < 0 || pe > np || pb > pe) return SGW_ERR_ARG;
+  const bool whole = pb == 0 && pe == np;
   cudaStream_t st = S(stream);
   double2* out = static_cast<double2*>(P0_tau);
+  // blocks of wedge points without pairs in a partial range are not written by the chains
+  if (!whole) CK(cudaMemsetAsync(out, 0, (size_t)c->nt * c->p_elems * sizeof(double2), st));
+  if (pb == pe) return SGW_OK;  // an empty range: the partial sum is zero
+  ContractionPlan& P = whole ? c->plan_p0 : c->plan_p0_part;
+  if (!c->use_tc) CKS(build_p0_plan(c, P, pb, pe));
   if (c->use_tc) {
     // tensor-core chains: TF32 head/tail products, FP32 accumulation, FP64 sums of the partial tiles
-    CKS(tc_polarization(c, static_cast<const double2*>(G_tau), out, st));
+    CKS(tc_polarization(c, static_cast<const double2*>(G_tau), out, pb, pe, st));
   } else if (c->p.precision == SGW_MIXED_FP32) {
     // G(tau) rounded to complex64 once; the chains accumulate in FP32, P0 is returned in FP64
     CKS(ensure_g32(c, (size_t)c->nt * c->g_elems));
     run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)c->nt * c->g_elems, st); });
-    CKS(polarization_impl<float2>(c, c->d_g32, c->d_V32[0], out, st, "_f32"));
+    CKS(polarization_impl<float2>(c, P, c->d_g32, c->d_V32[0], out, st, "_f32"));
   } else {
-    CKS(polarization_impl<double2>(c, static_cast<const double2*>(G_tau), c->d_V[0], out, st, ""));
+    CKS(polarization_impl<double2>(c, P, static_cast<const double2*>(G_tau), c->d_V[0], out, st, ""));
   }
   CK(cudaGetLastError());
   return SGW_OK;
+}
+
+extern "C" SGW_API sgw_status sgw_polarization(sgw_ctx* c, const void* G_tau, void* P0_tau, sgw_stream stream) {
+  if (!c) return SGW_ERR_ARG;
+  return polarization_range(c, G_tau, P0_tau, 0, (long long)c->nwedge * c->Nk, stream);
+}
+
+extern "C" SGW_API sgw_status sgw_polarization_pairs(sgw_ctx* c, const void* G_tau, void* P0_tau, long long pair_begin,
+                                                     long long pair_end, sgw_stream stream) {
+  if (!c) return SGW_ERR_ARG;
+  return polarization_range(c, G_tau, P0_tau, pair_begin, pair_end, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -1022,11 +1053,13 @@ extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P
 // ---------------------------------------------------------------------------
 // a7: self-energy
 // ---------------------------------------------------------------------------
-static sgw_status build_sigma_plan(sgw_ctx* c) {
-  ContractionPlan& P = c->plan_sigma;
-  if (P.built) return SGW_OK;
-  const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao;
-  const long long vs = vsize(c), np = (long long)nw * Nk;
+static sgw_status build_sigma_plan(sgw_ctx* c, ContractionPlan& P, long long pb, long long pe) {
+  if (P.built && P.pb == pb && P.pe == pe) return SGW_OK;
+  free_plan(P);
+  P.pb = pb;
+  P.pe = pe;
+  const int Nk = c->Nk, nt = c->nt, nao = c->nao;
+  const long long vs = vsize(c), np = pe - pb;
   const size_t budget = workspace_budget();
   int nc = (int)std::max<long long>(1, (long long)(budget * 0.8 / (2.0 * np * vs * sizeof(double2))));
   nc = std::min(nc, nt);
@@ -1037,12 +1070,13 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
   std::vector<BdItem> A((size_t)nt * np), B((size_t)nt * np);
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
-    for (long long p = 0; p < np; ++p) {
+    for (long long lp = 0; lp < np; ++lp) {
+      const long long p = pb + lp;
       const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
       int a = iv(k1, 0) - iv(k2, 0), b = iv(k1, 1) - iv(k2, 1), cc = iv(k1, 2) - iv(k2, 2);
       a = ((a % n1) + n1) % n1; b = ((b % n2) + n2) % n2; cc = ((cc % n3) + n3) % n3;
       const int q = (a * n2 + b) * n3 + cc;
-      const long long pos = (p * nc + tl) * vs;
+      const long long pos = (lp * nc + tl) * vs;
       BdItem x;
       x.x_off = p * vs;
       x.y_off = pos;
@@ -1050,7 +1084,7 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
       x.part = c->rep[k2];
       x.pad = 0;
       x.scale = z(1.0);
-      A[(size_t)t * np + p] = x;
+      A[(size_t)t * np + lp] = x;
       BdItem y;
       y.x_off = pos;
       y.y_off = pos;
@@ -1058,7 +1092,7 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
       y.part = c->rep[q];
       y.pad = 0;
       y.scale = z(1.0);
-      B[(size_t)t * np + p] = y;
+      B[(size_t)t * np + lp] = y;
     }
   }
   std::vector<GramUnit> units;
@@ -1079,11 +1113,12 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
     const int tl = t % nc;
     for (size_t b = 0; b < c->aob_off.size(); ++b) {
       const int w = c->aob_w[b], nb = c->aob_n[b], st = c->aob_start[b];
-      const long long p0 = (long long)w * Nk;
+      const long long p0 = std::max(pb, (long long)w * Nk), p1 = std::min(pe, (long long)(w + 1) * Nk);
+      if (p1 <= p0) continue;
       const size_t from = units.size();
       add_gram_block(units, tiles, base, nb, (long long)t * c->g_elems + c->aob_off[b],
-                     (p0 * nc + tl) * vs + (long long)st * nao, p0 * vs + (long long)st * nao, nao, nao, Nk,
-                     (long long)c->naux * nao, target, c->herm);
+                     ((p0 - pb) * nc + tl) * vs + (long long)st * nao, p0 * vs + (long long)st * nao, nao, nao,
+                     (int)(p1 - p0), (long long)c->naux * nao, target, c->herm);
       finalize_units(units, from, (long long)nc * vs, vs);
     }
   }
@@ -1096,14 +1131,18 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
     P.max_units_chunk = std::max(P.max_units_chunk, P.unit_start[t1] - P.unit_start[t0]);
   }
   P.fl_A_t = P.fl_B_t = P.fl_G_t = 0;
-  for (long long p = 0; p < np; ++p) {
+  for (long long p = pb; p < pe; ++p) {
     const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
     int a = iv(k1, 0) - iv(k2, 0), b = iv(k1, 1) - iv(k2, 1), cc = iv(k1, 2) - iv(k2, 2);
     a = ((a % n1) + n1) % n1; b = ((b % n2) + n2) % n2; cc = ((cc % n3) + n3) % n3;
     P.fl_A_t += 8.0 * c->naux * nao * (double)c->part_ao[c->rep[k2]].elems;
     P.fl_B_t += 8.0 * nao * nao * (double)c->part_aux[c->rep[(a * n2 + b) * n3 + cc]].elems;
   }
-  for (size_t b = 0; b < c->aob_n.size(); ++b) P.fl_G_t += 8.0 * Nk * (double)c->naux * nao * gram_elems(c, c->aob_n[b]);
+  for (size_t b = 0; b < c->aob_n.size(); ++b) {
+    const int w = c->aob_w[b];
+    const long long npw = std::max(0LL, std::min(pe, (long long)(w + 1) * Nk) - std::max(pb, (long long)w * Nk));
+    P.fl_G_t += 8.0 * npw * (double)c->naux * nao * gram_elems(c, c->aob_n[b]);
+  }
   CKS(upload(c, P.d_A, A));
   CKS(upload(c, P.d_B, B));
   CKS(upload(c, P.d_units, units));
@@ -1113,9 +1152,8 @@ static sgw_status build_sigma_plan(sgw_ctx* c) {
 }
 
 template <typename Z>
-static sgw_status self_energy_impl(sgw_ctx* c, const Z* G, const Z* Pt, const Z* V, double2* out, cudaStream_t st,
-                                   const char* tag) {
-  ContractionPlan& P = c->plan_sigma;
+static sgw_status self_energy_impl(sgw_ctx* c, const ContractionPlan& P, const Z* G, const Z* Pt, const Z* V,
+                                   double2* out, cudaStream_t st, const char* tag) {
   const int nt = c->nt, nao = c->nao, naux = c->naux, nc = P.nc;
   const long long vs = vsize(c), np = P.items_per_t;
   const size_t inter = (size_t)np * nc * vs;
@@ -1157,28 +1195,45 @@ static sgw_status self_energy_impl(sgw_ctx* c, const Z* G, const Z* Pt, const Z*
   return SGW_OK;
 }
 
-extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau,
-                                              sgw_stream stream) {
+static sgw_status self_energy_range(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau, long long pb,
+                                    long long pe, sgw_stream stream) {
   CKS(need_built(c));
   if (!c->have_v[1]) return c->fail(SGW_ERR_STATE, "self-energy pairs of V not loaded");
-  if (!G_tau || !P_tau || !Sigma_tau) return SGW_ERR_ARG;
-  if (!c->use_tc) CKS(build_sigma_plan(c));
+  const long long np = (long long)c->nwedge * c->Nk;
+  if (!G_tau || !P_tau || !Sigma_tau || pb < 0 || pe > np || pb > pe) return SGW_ERR_ARG;
+  const bool whole = pb == 0 && pe == np;
   cudaStream_t st = S(stream);
   double2* out = static_cast<double2*>(Sigma_tau);
+  if (!whole) CK(cudaMemsetAsync(out, 0, (size_t)c->nt * c->g_elems * sizeof(double2), st));
+  if (pb == pe) return SGW_OK;
+  ContractionPlan& P = whole ? c->plan_sigma : c->plan_sigma_part;
+  if (!c->use_tc) CKS(build_sigma_plan(c, P, pb, pe));
   if (c->use_tc) {
-    CKS(tc_self_energy(c, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau), out, st));
+    CKS(tc_self_energy(c, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau), out, pb, pe, st));
   } else if (c->p.precision == SGW_MIXED_FP32) {
     const size_t gn = (size_t)c->nt * c->g_elems, pn = (size_t)c->nt * c->p_elems;
     CKS(ensure_g32(c, gn + pn));
     run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(G_tau), c->d_g32, (long long)gn, st); });
     run(c, "convert", 0.0, 1, st, [&] { to_c64(static_cast<const double2*>(P_tau), c->d_g32 + gn, (long long)pn, st); });
-    CKS(self_energy_impl<float2>(c, c->d_g32, c->d_g32 + gn, c->d_V32[1], out, st, "_f32"));
+    CKS(self_energy_impl<float2>(c, P, c->d_g32, c->d_g32 + gn, c->d_V32[1], out, st, "_f32"));
   } else {
-    CKS(self_energy_impl<double2>(c, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau), c->d_V[1],
-                                  out, st, ""));
+    CKS(self_energy_impl<double2>(c, P, static_cast<const double2*>(G_tau), static_cast<const double2*>(P_tau),
+                                  c->d_V[1], out, st, ""));
   }
   CK(cudaGetLastError());
   return SGW_OK;
+}
+
+extern "C" SGW_API sgw_status sgw_self_energy(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau,
+                                              sgw_stream stream) {
+  if (!c) return SGW_ERR_ARG;
+  return self_energy_range(c, G_tau, P_tau, Sigma_tau, 0, (long long)c->nwedge * c->Nk, stream);
+}
+
+extern "C" SGW_API sgw_status sgw_self_energy_pairs(sgw_ctx* c, const void* G_tau, const void* P_tau, void* Sigma_tau,
+                                                    long long pair_begin, long long pair_end, sgw_stream stream) {
+  if (!c) return SGW_ERR_ARG;
+  return self_energy_range(c, G_tau, P_tau, Sigma_tau, pair_begin, pair_end, stream);
 }
 
 // ---------------------------------------------------------------------------

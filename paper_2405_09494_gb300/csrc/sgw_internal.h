@@ -173,6 +173,7 @@ struct TcPlan;  // tensor-core jobs of the chosen form (tc.cu)
 // Cached launch tables of one contraction (P0, Sigma or exchange), built once.
 struct ContractionPlan {
   bool built = false;
+  long long pb = 0, pe = 0;           // pair range [pb, pe) of the orientation's pair list it covers
   int nc = 0;                         // tau values per chunk
   long long items_per_t = 0;          // block-multiply items per tau value
   BdItem *d_A = nullptr, *d_B = nullptr;
@@ -229,7 +230,8 @@ struct sgw_ctx {
   float2* d_V32[2] = {nullptr, nullptr};  // complex64 copies for the chosen form (orientation 1 as
                                           // [pair][i][A][a] when the tensor-core chains are used)
   bool use_tc = false;                     // chosen form runs its chains on the tensor cores
-  sgw::TcPlan* tc = nullptr;
+  sgw::TcPlan* tc = nullptr;       // whole pair list
+  sgw::TcPlan* tc_part = nullptr;  // the last partial pair range asked for
   float2* d_g32 = nullptr;                 // complex64 tau series (chosen form)
   size_t g32_elems = 0;
   double2 *d_H0 = nullptr, *d_S = nullptr;  // packed [g_elems]
@@ -238,6 +240,7 @@ struct sgw_ctx {
 
   // cached launch tables
   sgw::ContractionPlan plan_p0, plan_sigma, plan_k, plan_rho;
+  sgw::ContractionPlan plan_p0_part, plan_sigma_part;  // the last partial pair range asked for
   std::vector<long long> plan_k_wbeg;  // per wedge point: first unit / tile of the exchange plan
   std::vector<long long> plan_k_tbeg;
   // per packed orbital element: block offset, block size, eps offset, row, column, wedge point
@@ -332,8 +335,11 @@ double gram_elems(const sgw_ctx* c, int nb);  // elements a Gram stage contracts
 bool tc_supported(const sgw_ctx* c);
 void tc_free(sgw_ctx* c);
 void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long long npairs, cudaStream_t st);
-sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStream_t st);
-sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, cudaStream_t st);
+// Contraction chains over the pairs [pb, pe) of orientation 0 (P0) or 1 (Sigma~): the partial sum
+// over those pairs, every output block written (blocks without pairs in the range are zero).
+sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long pb, long long pe, cudaStream_t st);
+sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, long long pb, long long pe,
+                          cudaStream_t st);
 }  // namespace sgw
 
 #define CK(call)                                                                               \

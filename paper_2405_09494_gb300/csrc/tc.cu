@@ -69,6 +69,7 @@ struct TcArgs {
 
 // Cached jobs of the tensor-core chains.
 struct TcPlan {
+  long long pb = 0, pe = 0;            // pair range [pb, pe) of the orientation's pair list
   bool built_p0 = false, built_sigma = false;
   long long unit_p0 = 0, unit_s = 0;   // split-K unit length of the Gram reductions (chunks)
   bool tuned_p0 = false, tuned_s = false;
@@ -916,8 +917,8 @@ int qindex(const sgw_ctx* c, int k1, int k2) {
   return (a * n2 + b) * n3 + cc;
 }
 
-long long tc_nc(const sgw_ctx* c) {
-  const long long vs = (long long)c->naux * c->nao * c->nao, np = (long long)c->nwedge * c->Nk;
+long long tc_nc(const sgw_ctx* c, long long np) {
+  const long long vs = (long long)c->naux * c->nao * c->nao;
   const char* s = std::getenv("SGW_WORKSPACE_GB");
   const double gb = s ? std::atof(s) : 24.0;
   const double budget = gb * 1e9;
@@ -958,14 +959,19 @@ bool tc_supported(const sgw_ctx* c) {
   return c->p.precision == SGW_MIXED_FP32 && c->nao % 2 == 0 && c->naux % 2 == 0 && c->nao <= 128;
 }
 
-void tc_free(sgw_ctx* c) {
-  if (!c->tc) return;
-  TcPlan& T = *c->tc;
+static void free_plan_tc(TcPlan*& t) {
+  if (!t) return;
+  TcPlan& T = *t;
   fr(T.d_vg); fr(T.d_gvg); fr(T.d_pg); fr(T.d_svg); fr(T.d_pvg); fr(T.d_sg); fr(T.d_pr); fr(T.d_sr);
   fr(T.d_prp); fr(T.d_srp);
   fr(T.d_ao_start); fr(T.d_ao_size); fr(T.d_ao_doff); fr(T.d_g_off); fr(T.d_ab_info); fr(T.d_ab_off);
-  delete c->tc;
-  c->tc = nullptr;
+  delete t;
+  t = nullptr;
+}
+
+void tc_free(sgw_ctx* c) {
+  free_plan_tc(c->tc);
+  free_plan_tc(c->tc_part);
 }
 
 // Interaction tensor for the tensor-core chains: orientation 0 keeps [pair][Q][i][j] (complex64),
@@ -981,10 +987,9 @@ void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long
 }
 
 // Gram jobs of P0 for split-K units of `unit` chunks (replaces the previous tables).
-static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
-  TcPlan& T = *c->tc;
+static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
   const int Nk = c->Nk, nt = c->nt, nao = c->nao, nc = T.nc_p0;
-  const long long np = (long long)c->nwedge * Nk;
+  const long long np = T.pe - T.pb;
   const int nch_g = (2 * nao * nao + 15) / 16;
   std::vector<TcJob> pg;
   std::vector<TcTile> pr;
@@ -998,10 +1003,14 @@ static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
     for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); T.prp_start[t] = prp.size(); }
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
       const int w = c->auxb_w[b], nb = c->auxb_n[b], s = c->auxb_start[b];
+      // the pairs of wedge point w inside the range (none: the block stays zero)
+      const long long p0 = std::max(T.pb, (long long)w * Nk), p1 = std::min(T.pe, (long long)(w + 1) * Nk);
+      if (p1 <= p0) continue;
       TcJob j{};
-      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
-      j.b_y = s; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
-      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, Nk, nch_g, unit, c->herm);
+      j.a_z = (int)(p0 - T.pb); j.a_dz = 1;  // X slabs are local pairs, V slabs global ones
+      j.b_y = s; j.b_z = (int)p0; j.b_dz = 1;
+      const GramTiles g = gram_interleaved(pg, slot0, kSlotD, j, s, nb, nc, nb, 64, (int)(p1 - p0), nch_g, unit,
+                                           c->herm);
       for (int t = t0; t < t1; ++t)
         gram_out_tiles(pr, g, s, nc, t - t0, s, nb, s, s, nb, (long long)t * c->p_elems + c->auxb_off[b], nb);
     }
@@ -1021,13 +1030,12 @@ static sgw_status build_p0_gram(sgw_ctx* c, long long unit) {
   return SGW_OK;
 }
 
-static sgw_status build_p0(sgw_ctx* c) {
-  TcPlan& T = *c->tc;
+static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   if (T.built_p0) return SGW_OK;
   CKS(tables_common(c, T));
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
-  const long long np = (long long)nw * Nk;
-  const int nc = (int)tc_nc(c);
+  const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
+  const int nc = (int)tc_nc(c, np);
   T.nc_p0 = nc;
   const int rows = naux * nao;
   T.mt_vg = (rows + 127) / 128;
@@ -1037,34 +1045,39 @@ static sgw_status build_p0(sgw_ctx* c) {
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
     T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size();
-    for (long long p = 0; p < np; ++p)
+    for (long long lp = 0; lp < np; ++lp)
       for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
+        const long long p = T.pb + lp;
         const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
         TcJob j{};
         j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
         j.b_z = (int)(((long long)0 * nt + t) * nw + c->rep[k2]);
         j.a_x = 0; j.b_x = 0; j.nslab = 1; j.nchunk = nch_o; j.a_dz = 0; j.b_dz = 0;
         j.m_rows = rows; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
-        j.out_off = ((long long)tl * np + p) * rows * nao + (long long)n0 * nao;  // Z'[A][j][c], column j = n0 + n
+        j.out_off = ((long long)tl * np + lp) * rows * nao + (long long)n0 * nao;  // Z'[A][j][c], column j = n0 + n
         vg.push_back(j);
         TcJob g = j;
-        g.a_z = (int)((long long)tl * np + p);
+        g.a_z = (int)((long long)tl * np + lp);
         g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
-        g.out_off = p * nc * (long long)rows * nao + (long long)tl * nao * nao + (long long)n0 * nao;  // X[p][Q][tl][i][j]
+        g.out_off = lp * nc * (long long)rows * nao + (long long)tl * nao * nao + (long long)n0 * nao;  // X[p][Q][tl][i][j]
         gvg.push_back(g);
       }
   }
   T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size();
   T.unit_p0 = unit_override() ? unit_override() : kUnitDefault;
   if (unit_override()) T.tuned_p0 = true;  // a fixed unit holds for the context's lifetime
-  CKS(build_p0_gram(c, T.unit_p0));
+  CKS(build_p0_gram(c, T, T.unit_p0));
   T.fl_vg = T.fl_gvg = T.fl_pg = 0;
-  for (long long p = 0; p < np; ++p) {
+  for (long long p = T.pb; p < T.pe; ++p) {
     T.fl_vg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k2[0][p]]].elems;
     T.fl_gvg += 8.0 * naux * nao * (double)c->part_ao[c->rep[c->pair_k1[0][p]]].elems;
   }
   // with Hermitian blocks the Gram stage needs their upper triangles only
-  for (size_t b = 0; b < c->auxb_n.size(); ++b) T.fl_pg += 8.0 * Nk * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) {
+    const int w = c->auxb_w[b];
+    const long long npw = std::max(0LL, std::min(T.pe, (long long)(w + 1) * Nk) - std::max(T.pb, (long long)w * Nk));
+    T.fl_pg += 8.0 * npw * (double)nao * nao * gram_elems(c, c->auxb_n[b]);
+  }
   CKS(up(c, T.d_vg, vg));
   CKS(up(c, T.d_gvg, gvg));
   T.built_p0 = true;
@@ -1072,8 +1085,7 @@ static sgw_status build_p0(sgw_ctx* c) {
 }
 
 // Gram jobs of Sigma~ for split-K units of `unit` chunks (replaces the previous tables).
-static sgw_status build_sigma_gram(sgw_ctx* c, long long unit) {
-  TcPlan& T = *c->tc;
+static sgw_status build_sigma_gram(sgw_ctx* c, TcPlan& T, long long unit) {
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux, nc = T.nc_s;
   const int nch_g = (2 * naux * nao + 15) / 16;
   std::vector<TcJob> sg;
@@ -1088,12 +1100,15 @@ static sgw_status build_sigma_gram(sgw_ctx* c, long long unit) {
     const long long slot0 = (long long)sg.size(), tile0 = (long long)sr.size();
     for (int t = t0; t < t1; ++t) { T.sg_start[t] = sg.size(); T.sr_start[t] = sr.size(); T.srp_start[t] = srp.size(); }
     for (int w = 0; w < nw; ++w) {
+      const long long p0 = std::max(T.pb, (long long)w * Nk), p1 = std::min(T.pe, (long long)(w + 1) * Nk);
+      if (p1 <= p0) continue;  // no pairs of this wedge point in the range: its blocks stay zero
       TcJob j{};
-      j.a_z = (int)((long long)w * Nk); j.a_dz = 1;
-      j.b_y = 0; j.b_z = (int)((long long)w * Nk); j.b_dz = 1;
+      j.a_z = (int)(p0 - T.pb); j.a_dz = 1;  // X2 slabs are local pairs, Vt slabs global ones
+      j.b_y = 0; j.b_z = (int)p0; j.b_dz = 1;
       // Hermitian Sigma~ blocks (closed frequency sets): tiles below the diagonal are left out and
       // the blocks' lower triangles filled by conjugate transposition after the reduction
-      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, Nk, nch_g, unit, c->herm);
+      const GramTiles g = gram_interleaved(sg, slot0, T.slot_s, j, 0, nao, nc, nao, 64, (int)(p1 - p0), nch_g, unit,
+                                           c->herm);
       for (int t = t0; t < t1; ++t)
         for (size_t b = 0; b < c->aob_off.size(); ++b) {
           if (c->aob_w[b] != w) continue;
@@ -1116,13 +1131,12 @@ static sgw_status build_sigma_gram(sgw_ctx* c, long long unit) {
   return SGW_OK;
 }
 
-static sgw_status build_sigma(sgw_ctx* c) {
-  TcPlan& T = *c->tc;
+static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
   if (T.built_sigma) return SGW_OK;
   CKS(tables_common(c, T));
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
-  const long long np = (long long)nw * Nk;
-  const int nc = (int)tc_nc(c);
+  const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
+  const int nc = (int)tc_nc(c, np);
   T.nc_s = nc;
   T.slot_s = kSlotD;
   const long long vs = (long long)naux * nao * nao;
@@ -1154,7 +1168,8 @@ static sgw_status build_sigma(sgw_ctx* c) {
   for (int t = 0; t < nt; ++t) {
     const int tl = t % nc;
     T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size();
-    for (long long p = 0; p < np; ++p) {
+    for (long long lp = 0; lp < np; ++lp) {
+      const long long p = T.pb + lp;
       const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
       for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
         TcJob j{};
@@ -1162,7 +1177,7 @@ static sgw_status build_sigma(sgw_ctx* c) {
         j.b_z = (int)((long long)t * nw + c->rep[k2]);
         j.nslab = 1; j.nchunk = nch_o;
         j.m_rows = rows_v; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
-        j.out_off = ((long long)tl * np + p) * vs + (long long)n0 * naux;  // X1T[i][b][A], column b = n0 + n
+        j.out_off = ((long long)tl * np + lp) * vs + (long long)n0 * naux;  // X1T[i][b][A], column b = n0 + n
         svg.push_back(j);
       }
       const int wq = c->rep[qindex(c, k1, k2)];
@@ -1170,13 +1185,13 @@ static sgw_status build_sigma(sgw_ctx* c) {
         const int s = info[3 * b], nb = info[3 * b + 1], d = info[3 * b + 2];
         for (int n0 = 0; n0 < nb; n0 += 64) {
           TcJob v{};
-          v.a_y = 0; v.a_z = (int)((long long)tl * np + p);
+          v.a_y = 0; v.a_z = (int)((long long)tl * np + lp);
           v.a_x = 2 * s - d;
           v.b_y = n0; v.b_z = tl * ninst + b;
           v.b_x = 0;
           v.nslab = 1; v.nchunk = (d + 2 * nb + 15) / 16;
           v.m_rows = rows_x; v.n_valid = std::min(64, nb - n0); v.n_mma = round16(v.n_valid);
-          v.out_off = p * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
+          v.out_off = lp * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
           pvg.push_back(v);
         }
       }
@@ -1185,24 +1200,37 @@ static sgw_status build_sigma(sgw_ctx* c) {
   T.svg_start[nt] = svg.size(); T.pvg_start[nt] = pvg.size();
   T.unit_s = unit_override() ? unit_override() : kUnitDefault;
   if (unit_override()) T.tuned_s = true;
-  CKS(build_sigma_gram(c, T.unit_s));
+  CKS(build_sigma_gram(c, T, T.unit_s));
   T.fl_svg = T.fl_pvg = T.fl_sg = 0;
-  for (long long p = 0; p < np; ++p) {
+  for (long long p = T.pb; p < T.pe; ++p) {
     const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
     T.fl_svg += 8.0 * naux * nao * (double)c->part_ao[c->rep[k2]].elems;
     T.fl_pvg += 8.0 * nao * nao * (double)c->part_aux[c->rep[qindex(c, k1, k2)]].elems;
   }
   // with Hermitian blocks the Gram stage needs their upper triangles only
-  for (size_t b = 0; b < c->aob_n.size(); ++b) T.fl_sg += 8.0 * Nk * (double)naux * nao * gram_elems(c, c->aob_n[b]);
+  for (size_t b = 0; b < c->aob_n.size(); ++b) {
+    const int w = c->aob_w[b];
+    const long long npw = std::max(0LL, std::min(T.pe, (long long)(w + 1) * Nk) - std::max(T.pb, (long long)w * Nk));
+    T.fl_sg += 8.0 * npw * (double)naux * nao * gram_elems(c, c->aob_n[b]);
+  }
   CKS(up(c, T.d_svg, svg));
   CKS(up(c, T.d_pvg, pvg));
   T.built_sigma = true;
   return SGW_OK;
 }
 
-static sgw_status ensure_plan(sgw_ctx* c) {
-  if (!c->tc) c->tc = new TcPlan();
-  return SGW_OK;
+// The plan of the pair range [pb, pe): the whole pair list has its own; one partial range is kept
+// (a rank of a partitioned run asks for the same range every time).
+static TcPlan& plan_for(sgw_ctx* c, long long pb, long long pe) {
+  const bool whole = pb == 0 && pe == (long long)c->nwedge * c->Nk;
+  TcPlan*& t = whole ? c->tc : c->tc_part;
+  if (t && (t->pb != pb || t->pe != pe)) free_plan_tc(t);
+  if (!t) {
+    t = new TcPlan();
+    t->pb = pb;
+    t->pe = pe;
+  }
+  return *t;
 }
 
 static bool capturing(cudaStream_t st) {
@@ -1246,22 +1274,22 @@ static sgw_status tune_unit(sgw_ctx* c, cudaStream_t st, const char* what, long 
   return SGW_OK;
 }
 
-sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStream_t st) {
-  CKS(ensure_plan(c));
-  CKS(build_p0(c));
-  TcPlan& T = *c->tc;
+sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long pb, long long pe, cudaStream_t st) {
+  TcPlan& T = plan_for(c, pb, pe);
+  CKS(build_p0(c, T));
   const int nt = c->nt, nw = c->nwedge, nao = c->nao, naux = c->naux, Nk = c->Nk, nc = T.nc_p0;
-  const long long np = (long long)nw * Nk, vs = (long long)naux * nao * nao;
+  // np: pairs of the range (intermediate slabs); npg: the whole pair list (V slabs)
+  const long long np = T.pe - T.pb, npg = (long long)nw * Nk, vs = (long long)naux * nao * nao;
   const long long inter = (long long)nc * np * vs;  // complex64 elements
   const long long gop = 2LL * nt * nw * 4 * nao * 2 * nao;  // floats
   const bool tune = !T.tuned_p0 && autotune_enabled() && !capturing(st);
   long long max_units = T.max_units_p0;
   if (tune) {  // partial tiles for the candidate with the most units
     for (long long cand : kUnitCandidates) {
-      CKS(build_p0_gram(c, cand));
+      CKS(build_p0_gram(c, T, cand));
       max_units = std::max(max_units, T.max_units_p0);
     }
-    CKS(build_p0_gram(c, T.unit_p0));
+    CKS(build_p0_gram(c, T, T.unit_p0));
   }
   const long long b_z = al256(inter * 8), b_x = al256(inter * 8), b_g = al256(gop * 4),
                   b_p = al256(max_units * kSlotD * 8);
@@ -1277,13 +1305,13 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   });
   CUtensorMap mV, mZ, mG;
   const long long rows = (long long)naux * nao;
-  CKS(make_map(c, &mV, c->d_V32[0], 2 * nao, rows, np, 8LL * nao, vs * 8, 128));
+  CKS(make_map(c, &mV, c->d_V32[0], 2 * nao, rows, npg, 8LL * nao, vs * 8, 128));
   CKS(make_map(c, &mZ, Zp, 2 * nao, rows, (long long)nc * np, 8LL * nao, vs * 8, 128));
   CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 2LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, 64));
   // Gram operands: rows Q, contracted (i, j) re/im
   CUtensorMap mXg, mVg;
   CKS(make_map(c, &mXg, X, 2LL * nao * nao, (long long)naux * nc, np, 8LL * nao * nao, (long long)nc * vs * 8, 32));
-  CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, np, 8LL * nao * nao, vs * 8, 64));
+  CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, npg, 8LL * nao * nao, vs * 8, 64));
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
@@ -1325,7 +1353,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
         reduce();
         return SGW_OK;
       };
-      CKS(tune_unit(c, st, "P0", T.unit_p0, [&](long long u) { return build_p0_gram(c, u); }, both));
+      CKS(tune_unit(c, st, "P0", T.unit_p0, [&](long long u) { return build_p0_gram(c, T, u); }, both));
       T.tuned_p0 = true;
     }
     run(c, "p0_gram_tc", T.fl_pg * ntc, 1, st, [&] { s3 = gemm(); });
@@ -1336,12 +1364,12 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, cudaStrea
   return lower_from_upper(c, 1, out, st);
 }
 
-sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, cudaStream_t st) {
-  CKS(ensure_plan(c));
-  CKS(build_sigma(c));
-  TcPlan& T = *c->tc;
+sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, long long pb, long long pe,
+                          cudaStream_t st) {
+  TcPlan& T = plan_for(c, pb, pe);
+  CKS(build_sigma(c, T));
   const int nt = c->nt, nw = c->nwedge, nao = c->nao, naux = c->naux, Nk = c->Nk, nc = T.nc_s;
-  const long long np = (long long)nw * Nk, vs = (long long)naux * nao * nao;
+  const long long np = T.pe - T.pb, npg = (long long)nw * Nk, vs = (long long)naux * nao * nao;
   const long long inter = (long long)nc * np * vs;
   const long long gop = 1LL * nt * nw * 4 * nao * 2 * nao;
   const long long pop = (long long)nc * T.ninst * 4 * T.pt_rows * T.pt_k;
@@ -1349,10 +1377,10 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   long long max_units = T.max_units_s;
   if (tune) {  // partial tiles for the candidate with the most units
     for (long long cand : kUnitCandidates) {
-      CKS(build_sigma_gram(c, cand));
+      CKS(build_sigma_gram(c, T, cand));
       max_units = std::max(max_units, T.max_units_s);
     }
-    CKS(build_sigma_gram(c, T.unit_s));
+    CKS(build_sigma_gram(c, T, T.unit_s));
   }
   const long long b_1 = al256(inter * 8), b_2 = al256(inter * 8), b_g = al256(gop * 4), b_pp = al256(pop * 4),
                   b_p = al256(max_units * T.slot_s * 8);
@@ -1369,13 +1397,13 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
   });
   CUtensorMap mVt, mG, mX1, mP, mX2g, mVtg;
   const long long rows_v = (long long)nao * naux;
-  CKS(make_map(c, &mVt, c->d_V32[1], 2 * nao, rows_v, np, 8LL * nao, vs * 8, 128));
+  CKS(make_map(c, &mVt, c->d_V32[1], 2 * nao, rows_v, npg, 8LL * nao, vs * 8, 128));
   CKS(make_map4(c, &mG, Gop, 2 * nao, nao, 1LL * nt * nw, 8LL * nao, 8LL * nao * nao, 32LL * nao * nao, 64));
   CKS(make_map(c, &mX1, X1, 2LL * naux, (long long)nao * nao, (long long)nc * np, 8LL * naux, vs * 8, 128));
   CKS(make_map4(c, &mP, Pop, T.pt_k, T.pt_rows, (long long)nc * T.ninst, 4LL * T.pt_k, 4LL * T.pt_k * T.pt_rows,
                 16LL * T.pt_k * T.pt_rows, 64));
   CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, (long long)nao * nc, np, 8LL * naux * nao, (long long)nc * vs * 8, 32));
-  CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, np, 8LL * naux * nao, vs * 8, 64));
+  CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, npg, 8LL * naux * nao, vs * 8, 64));
   for (int t0 = 0; t0 < nt; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     run(c, "tc_prep", 0.0, 1, st, [&] {
@@ -1423,7 +1451,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
         reduce();
         return SGW_OK;
       };
-      CKS(tune_unit(c, st, "Sigma", T.unit_s, [&](long long u) { return build_sigma_gram(c, u); }, both));
+      CKS(tune_unit(c, st, "Sigma", T.unit_s, [&](long long u) { return build_sigma_gram(c, T, u); }, both));
       T.tuned_s = true;
     }
     run(c, "sigma_gram_tc", T.fl_sg * ntc, 1, st, [&] { s3 = gemm(); });

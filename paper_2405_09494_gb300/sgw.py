@@ -26,7 +26,8 @@ EXPORTS = [
     "sgw_get_wedge", "sgw_get_blocks", "sgw_get_pairs", "sgw_get_basis", "sgw_load_one_body", "sgw_load_v",
     "sgw_g0", "sgw_polarization", "sgw_screened_interaction", "sgw_self_energy", "sgw_hartree_fock", "sgw_dyson",
     "sgw_energy", "sgw_iterate", "sgw_unfold", "sgw_host_grid", "sgw_host_symmetry", "sgw_profile_enable",
-    "sgw_profile_read", "sgw_screened_interaction_noalloc", "sgw_set_wait_limit",
+    "sgw_profile_read", "sgw_screened_interaction_noalloc", "sgw_set_wait_limit", "sgw_polarization_pairs",
+    "sgw_self_energy_pairs",
 ]
 
 
@@ -90,6 +91,8 @@ def load_library(path: str = LIB_PATH):
         "sgw_load_v": ([vp, i, ll, ll, vp, vp], i),
         "sgw_g0": ([vp, ctypes.POINTER(d), vp, vp], i),
         "sgw_polarization": ([vp, vp, vp, vp], i),
+        "sgw_polarization_pairs": ([vp, vp, vp, ll, ll, vp], i),
+        "sgw_self_energy_pairs": ([vp, vp, vp, vp, ll, ll, vp], i),
         "sgw_screened_interaction": ([vp, vp, vp, vp], i),
         "sgw_self_energy": ([vp, vp, vp, vp, vp], i),
         "sgw_hartree_fock": ([vp, vp, vp, vp], i),
@@ -255,6 +258,11 @@ def sgw_polarization(ctx, G_tau, P0_tau, stream=None):
     _check(load_library().sgw_polarization(ctx, _ptr(G_tau), _ptr(P0_tau), _stream(stream)), ctx)
 
 
+def sgw_polarization_pairs(ctx, G_tau, P0_tau, pair_begin, pair_end, stream=None):
+    _check(load_library().sgw_polarization_pairs(ctx, _ptr(G_tau), _ptr(P0_tau), int(pair_begin), int(pair_end),
+                                                 _stream(stream)), ctx)
+
+
 def sgw_screened_interaction(ctx, P0_tau, P_tau, stream=None):
     _check(load_library().sgw_screened_interaction(ctx, _ptr(P0_tau), _ptr(P_tau), _stream(stream)), ctx)
 
@@ -270,6 +278,11 @@ def sgw_screened_interaction_noalloc(ctx, P0_tau, P_tau, stream=None):
 
 def sgw_self_energy(ctx, G_tau, P_tau, Sigma_tau, stream=None):
     _check(load_library().sgw_self_energy(ctx, _ptr(G_tau), _ptr(P_tau), _ptr(Sigma_tau), _stream(stream)), ctx)
+
+
+def sgw_self_energy_pairs(ctx, G_tau, P_tau, Sigma_tau, pair_begin, pair_end, stream=None):
+    _check(load_library().sgw_self_energy_pairs(ctx, _ptr(G_tau), _ptr(P_tau), _ptr(Sigma_tau), int(pair_begin),
+                                                int(pair_end), _stream(stream)), ctx)
 
 
 def sgw_hartree_fock(ctx, G_tau, Sigma_hf, stream=None):
