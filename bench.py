@@ -1,21 +1,31 @@
 """Benchmark: one self-consistent GW iteration of the symmetry-adapted hot path on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c2]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c4]
 
 A step is one full pass of the hot path on the workload: P0 (Eq. (P0)) ->
 P = [I - P0]^{-1} P0 (Eq. (P02P)) -> Sigma~ (Eq. (sigma)) -> Sigma_HF
 (Eq. (sigma_hf)) -> damping -> Dyson with the chemical-potential search
-(Eq. (dyson)), through the C ABI (sgw_iterate with one pass).  Inputs (V, H0,
-S) are resident in HBM; each timed step is bracketed by CUDA events on the
-launching stream, with a 512 MiB buffer written between steps to flush L2.
+(Eq. (dyson)), through the C ABI (sgw_iterate with one pass, replayed from one
+CUDA graph).  Inputs (V, H0, S) are resident in HBM; each timed step is
+bracketed by CUDA events on the launching stream, with a 512 MiB buffer written
+between steps (the workload's own operands are several GB, far above L2).
 The metric is the iteration time in seconds (lower is better).
 
-ours      : prints one JSON line with the device-timed value, the end-to-end
+The default workload is c4 (diamond Fd-3m, 4x4x4 mesh, nao 52, naux 300,
+150 tau), the largest whose loop fits a benchmark run: its chosen form (the
+headline) takes about 2.6 s per pass; workload c5 (nao 104, naux 600, 200 tau)
+takes about a minute per chosen-form pass and tens of minutes per plain pass.
+The plain complex128 form runs one pass from the chosen form's state: its time
+is reported beside the headline, and its result fixes the chosen form's error
+per quantity.
+
+ours      : one JSON line: the chosen form's device-timed value, the end-to-end
             value through host buffers, the roofline of the dominant kernel,
-            clocks sampled during the timed region and the oracle's CPU time
-            on a bounded sample of the same workload.
+            clocks sampled during the timed region, the plain form's pass, the
+            error per quantity, and the oracle's CPU time.
 reference : the oracle (plain CPU code of the method) on the host cores, on a
-            bounded sample of the same workload, scaled to one iteration.
+            bounded sample of the same workload scaled to one pass (the whole
+            pass where it fits).
 """
 from __future__ import annotations
 
@@ -33,19 +43,24 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "scGW iteration time (s) and TFLOP/s vs tensor peak, mixed vs FP64 at stated error"
+DEFAULT_CONFIG = "c4"
+NOT_C5 = ("c5 (rocksalt, nao 104, naux 600, 200 tau) takes about a minute per chosen-form pass and tens of "
+          "minutes per plain pass, beyond a benchmark run; its loop is recorded separately")
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz
-# TF32 tensor peak from the measured bf16 burst (MEASURED_PEAKS.json) and the nominal 1.1 / 2.25 ratio;
-# the chosen form spends three TF32 products per FP32-accurate product
-TF32_X3_PEAK_TFLOPS = 1907.2 * 1.1 / 2.25 / 3
-# the same from the sustained bf16 figure, for kernels inside iterations longer than a second
-TF32_X3_SUSTAINED_TFLOPS = 1734.0 * 1.1 / 2.25 / 3
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
-HBM_PEAK_GBS = 6657.6  # measured copy bandwidth (MEASURED_PEAKS.json)
-# DRAM bytes (read + write) of one launch of a kernel class on a workload, from one ncu capture
-# (profiles/k_bd_mult_fp64_c2.md, profiles/k_tc_persist_c2.md); reported as the roofline's traffic
-# while the kernel is unchanged.
-DRAM_TRAFFIC_BYTES = {("c2", "sigma_pvg"): 4654034944 + 2777765888,
-                      ("c2", "sigma_pvg_tc"): 1556365056 + 1358604800}
+
+
+def measured_peaks():
+    """HBM copy GB/s and bf16 TFLOP/s (burst, sustained) measured on this pool (MEASURED_PEAKS.json);
+    the machine's fallback figures when the file is absent."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), \
+            "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, 1700.0, "of fallback"
 
 
 def _args():
@@ -54,13 +69,13 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed", help="comma list of plain, mixed")
-    ap.add_argument("--profile-steps", type=int, default=None, help="profiled passes (default: --steps)")
+    ap.add_argument("--forms", default="mixed,plain",
+                    help="comma list; the first is timed over --steps, a second gets one pass from its state")
+    ap.add_argument("--profile-steps", type=int, default=None, help="profiled passes (default: min(steps, 3))")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--check-errors", action="store_true",
-                    help="with --forms mixed: one FP64 pass from the chosen form's state for its error")
+    ap.add_argument("--no-errors", action="store_true", help="skip the second form's pass and the error check")
     return ap.parse_args()
 
 
@@ -118,59 +133,8 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# oracle on the host cores (bounded sample of the same workload)
+# oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg, repeats=1):
-    """Time the oracle on one q of P0 (+ its W solve) and one k of Sigma, scaled by N_k, plus HF and Dyson.
-
-    The oracle's full-zone work is the same for every q (P0, W) and every k (Sigma), so
-    N_k x (sample) + (HF + Dyson with the mu search) is its iteration time.
-    """
-    import numpy as np
-
-    from oracle import grid, gw
-    from paper_2405_09494_gb300 import synth
-
-    sysm = synth.System(cfg)
-    Vf = sysm.V
-    tau = grid.tau_nodes(cfg.beta, cfg.ntau)
-    TF = grid.forward_map(cfg.mats_f, cfg.beta, cfg.ntau, "F")
-    TB = grid.forward_map(cfg.mats_b, cfg.beta, cfg.ntau, "B")
-    ops = dict(TF=TF, TFbar=grid.backward_map(TF), TB=TB, TBbar=grid.backward_map(TB),
-               nu_f=grid.matsubara_nu(cfg.mats_f, cfg.beta, "F"))
-    mu = gw.mu_noninteracting(sysm.H0, sysm.S, cfg.beta, cfg.n_elec)
-    G = gw.g0_tau(sysm.H0, sysm.S, mu, cfg.beta, tau)
-    cache = {}
-
-    def V(a, b):
-        if (a, b) not in cache:
-            cache[(a, b)] = Vf(a, b)
-        return cache[(a, b)]
-
-    Nk = cfg.nkpts
-    # warm the V cache for the sampled pairs outside the timed region (input generation, not the method)
-    for k in range(Nk):
-        for kp in range(Nk):
-            V(k, kp)
-    times = []
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        P0 = gw.polarization(G, V, cfg.nk, cfg.spin, cfg.loop_sign, qs=[1])
-        P, _, _ = gw.screened_interaction(P0[1:2], TB, ops["TBbar"])
-        Pfull = np.zeros_like(P0)
-        Pfull[1] = P[0]
-        t1 = time.perf_counter()
-        gw.self_energy(G, Pfull, V, cfg.nk, ks=[0])
-        t2 = time.perf_counter()
-        gam = gw.density_matrix(G)
-        Shf, _, _ = gw.hartree_fock(gam, V, cfg.nk, cfg.spin)
-        Sig = np.zeros_like(G)
-        gw.dyson(sysm.H0, sysm.S, Shf, Sig, mu, ops, cfg.n_elec, cfg.spin, search_mu=True)
-        t3 = time.perf_counter()
-        times.append(Nk * (t1 - t0) + Nk * (t2 - t1) + (t3 - t2))
-    return min(times), blas_threads()
-
-
 def blas_threads() -> int:
     """Threads the oracle's BLAS runs on: the thread-count variables numpy's BLAS reads at load
     (the smallest one set; torchrun sets OMP_NUM_THREADS=1), else every host core."""
@@ -185,21 +149,135 @@ def blas_threads() -> int:
     return min(vals) if vals else (os.cpu_count() or 1)
 
 
+def _oracle_inputs(cfg, system=None):
+    import numpy as np
+
+    from oracle import grid, gw
+    from paper_2405_09494_gb300 import synth
+
+    sysm = system if system is not None else synth.System(cfg)
+    cache = {}
+
+    def V(a, b):
+        if (a, b) not in cache:
+            v = sysm.V(a, b)
+            cache[(a, b)] = v if isinstance(v, np.ndarray) else v.cpu().numpy()
+        return cache[(a, b)]
+
+    tau = grid.tau_nodes(cfg.beta, cfg.ntau)
+    TF = grid.forward_map(cfg.mats_f, cfg.beta, cfg.ntau, "F")
+    TB = grid.forward_map(cfg.mats_b, cfg.beta, cfg.ntau, "B")
+    ops = dict(TF=TF, TFbar=grid.backward_map(TF), TB=TB, TBbar=grid.backward_map(TB),
+               nu_f=grid.matsubara_nu(cfg.mats_f, cfg.beta, "F"), tau=tau)
+    mu = gw.mu_noninteracting(sysm.H0, sysm.S, cfg.beta, cfg.n_elec)
+    G = gw.g0_tau(sysm.H0, sysm.S, mu, cfg.beta, tau)
+    return sysm, V, ops, mu, G
+
+
+def full_pass_fits(cfg) -> bool:
+    """Whether one full-zone oracle pass takes about a minute or less (workloads c1, c2 and smaller)."""
+    return cfg.nkpts ** 2 * cfg.naux * cfg.nao ** 2 * cfg.ntau <= 27 ** 2 * 100 * 18 ** 2 * 50
+
+
+# the oracle's bisection of [-20, 20] to |N - N_e| <= 1e-11: about log2(40 N' / 1e-11) trials, N' ~ 10
+DYSON_TRIALS = 45
+
+
+def oracle_sample(cfg, system=None):
+    """One pass of the oracle (full zone, no symmetry, complex128) on the host cores, in seconds.
+
+    Workloads where it fits: the whole pass from G0 (P0 -> W -> Sigma~, HF -> Dyson with the
+    bisection of mu).  Larger ones: a bounded sample scaled by the counts of the full pass:
+      P0 at one (q, tau) over all k                 x N_k n_tau
+      the W solve at one q, every frequency         x N_k
+      Sigma~ at one (k, tau) over all q             x N_k n_tau
+      Hartree-Fock at one k                         x N_k
+      one Dyson evaluation (every k and frequency)  x DYSON_TRIALS + 1
+    Input generation (V pairs, G0) is outside the timed region.
+    Returns (seconds, description of the sample).
+    """
+    import numpy as np
+
+    from oracle import gw
+
+    sysm, V, ops, mu, G = _oracle_inputs(cfg, system)
+    Nk, nt, nk = cfg.nkpts, cfg.ntau, cfg.nk
+    if full_pass_fits(cfg):
+        for k1 in range(Nk):
+            for k2 in range(Nk):
+                V(k1, k2)
+        t0 = time.perf_counter()
+        gw.scgw_iteration(sysm.H0, sysm.S, V, nk, G, mu, ops, cfg.n_elec, cfg.spin, cfg.loop_sign, search_mu=True,
+                          Sigma_old=np.zeros_like(G), Sigma_hf_old=np.zeros_like(G[:, 0]), damping=cfg.damping)
+        return time.perf_counter() - t0, "one whole oracle pass (full zone) from G0"
+    q, k, t = 1, 0, nt // 2
+    for kk in range(Nk):  # the pairs of the sample (input generation, not timed)
+        V(kk, gw.kadd(nk, kk, q)); V(gw.kadd(nk, kk, q), kk); V(k, kk); V(kk, k); V(kk, kk)
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(1, nt, cfg.naux, cfg.naux)) * (0.01 / cfg.naux)
+    P0q = (X + X.transpose(0, 1, 3, 2)).astype(np.complex128)  # a P0 series for the W-solve timing
+    Pfull = np.zeros((Nk, 1, cfg.naux, cfg.naux), np.complex128)
+    Pfull[:, 0] = P0q[0, t]
+    gam = gw.density_matrix(G)
+    Sw = np.zeros((Nk, len(cfg.mats_f), cfg.nao, cfg.nao), np.complex128)
+    Shf0 = np.zeros_like(G[:, 0])
+    c = {}
+    t0 = time.perf_counter()
+    gw.polarization(G, V, nk, cfg.spin, cfg.loop_sign, qs=[q], taus=[t])
+    c["p0"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gw.screened_interaction(P0q, ops["TB"], ops["TBbar"])
+    c["w"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gw.self_energy(G[:, t:t + 1], Pfull, V, nk, ks=[k])
+    c["sigma"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gw.hartree_fock(gam, V, nk, cfg.spin, ks=[k])
+    c["hf"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gw.dyson_matsubara(sysm.H0, sysm.S, Shf0, Sw, mu, ops["nu_f"])
+    c["dyson"] = time.perf_counter() - t0
+    total = Nk * nt * (c["p0"] + c["sigma"]) + Nk * (c["w"] + c["hf"]) + (DYSON_TRIALS + 1) * c["dyson"]
+    desc = (f"extrapolated: P0 at one (q, tau) and Sigma~ at one (k, tau) over all {Nk} pairs (x {Nk * nt}), "
+            f"the W solve at one q (x {Nk}), Hartree-Fock at one k (x {Nk}), one Dyson evaluation "
+            f"(x {DYSON_TRIALS + 1}); sample times (s): " + ", ".join(f"{a} {b:.3f}" for a, b in c.items()))
+    return total, desc
+
+
+def single_core_c1():
+    """The whole c1 oracle pass on one core (BLAS limited to one thread in a child process)."""
+    code = ("import time, bench; from paper_2405_09494_gb300 import configs; "
+            "t, _ = bench.oracle_sample(configs.get('c1')); print(t)")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=600)
+        return float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def run_reference(args, rank, world):
-    from paper_2405_09494_gb300 import configs
+    from paper_2405_09494_gb300 import configs, synth
 
     if rank != 0:
         return
     cfg = configs.get(args.config)
-    val, cores = oracle_sample(cfg, repeats=max(1, args.steps))
+    system = synth.System(cfg)
+    vals, desc = [], ""
+    for i in range(max(0, args.warmup) + max(1, args.steps)):
+        v, desc = oracle_sample(cfg, system)
+        if i >= args.warmup:
+            vals.append(v)
+    val = statistics.median(vals)
+    cores = blas_threads()
     line = {
         "metric": METRIC, "impl": "reference", "value": val, "unit": "s/iteration", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": cfg.description, "name": cfg.name, "form": "oracle (full zone, no symmetry)"},
         "cpu_baseline": {"value": val, "unit": "s/iteration", "cores": cores, "kind": "oracle",
-                         "sample": f"P0 + W at 1 of {cfg.nkpts} q and Sigma at 1 of {cfg.nkpts} k, scaled by "
-                                   f"{cfg.nkpts}; HF and Dyson with mu search in full"},
+                         "sample": desc + "; median over the steps"},
         "e2e": {"value": val, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -258,7 +336,7 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     # per-kernel breakdown: the same passes with CUDA events around every launch (no graph)
     sgw.sgw_profile_read(ctx, reset=True)
     sgw.sgw_profile_enable(ctx, True)
-    nprof = args.profile_steps if args.profile_steps is not None else args.steps
+    nprof = args.profile_steps if args.profile_steps is not None else min(args.steps, 3)
     for _ in range(nprof):
         flush.zero_()
         torch.cuda.synchronize(dev)
@@ -298,89 +376,89 @@ def _time_form(sess, cfg, args, dev, local, flush, world, e2e=False):
     return out
 
 
-def _algorithmic_bytes(dom, cfg, npairs, steps):
-    """Bytes one launch of the class must move: sigma_pvg reads X1 and writes X2, each
-    npairs x ntau x naux x nao^2 complex (16 bytes in the plain form, 8 in the chosen form), per
-    step; None for the other classes."""
-    if not dom.startswith("sigma_pvg"):
-        return None
-    esize = 16 if dom == "sigma_pvg" else 8
-    return 2.0 * npairs * cfg.ntau * cfg.naux * cfg.nao * cfg.nao * esize * steps
-
-
-def _roofline(prof, workload=None, cfg=None, npairs=None, steps=1, step_s=0.0):
-    """Roofline of the kernel class with the most device time.  Its arithmetic intensity (flops per
-    algorithmic byte, where the bytes are known) against the pipe's balance point decides the bound:
-    below it the kernel is measured against the HBM copy bandwidth, above it against the peak of
-    the pipe it runs on."""
-    compute = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(compute, key=lambda k: compute[k][0])
-    ms, gf, nl = compute[dom]
-    achieved = (gf / nl) / (ms / nl)  # GFLOP per launch / ms per launch = TFLOP/s
-    traffic = DRAM_TRAFFIC_BYTES.get((workload, dom))
-    if dom.endswith("_tc"):
-        if step_s > 1.0:
-            bound, peak, note = "tensor", TF32_X3_SUSTAINED_TFLOPS, (
-                "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 sustained "
-                "1734 TF/s x nominal TF32/BF16 ratio 1.1/2.25 = 848 TF/s, / 3 = 283 TF/s (of measured; the "
-                "iteration lasts over a second)")
-        else:
-            bound, peak, note = "tensor", TF32_X3_PEAK_TFLOPS, (
-                "TF32 tensor peak / 3 (three TF32 products per FP32-accurate product): measured bf16 burst "
-                "1907.2 TF/s x nominal TF32/BF16 ratio 1.1/2.25 = 932 TF/s, / 3 = 311 TF/s (of measured)")
-        nbytes = _algorithmic_bytes(dom, cfg, npairs, steps) if cfg is not None and npairs else None
-        if nbytes:
-            ai = gf * 1e9 / nbytes
-            if ai < peak * 1e12 / (HBM_PEAK_GBS * 1e9):
-                gbs = (nbytes / nl) / (ms / nl * 1e-3) / 1e9
-                return {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                        "frac": gbs / HBM_PEAK_GBS, "traffic": traffic,
-                        "algorithmic_bytes_per_launch": nbytes / nl, "flop_per_byte": ai,
-                        "tflops": achieved, "tflops_frac_of_tensor_peak": achieved / peak,
-                        "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); the kernel's "
-                                     f"{ai:.1f} flop/byte is below the balance point of {note.split(':')[0]} "
-                                     f"({peak * 1e3 / HBM_PEAK_GBS:.1f} flop/byte)"}
-    elif dom.endswith("_f32"):
-        bound, peak, note = "alu", FP32_PEAK_TFLOPS, (
-            "FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived; a probe measured 70.4)")
-    else:
-        bound, peak, note = "alu", FP64_PEAK_TFLOPS, (
-            "FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived; a DFMA probe measured 1.20)")
-    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_note": note}
-
-
-def _kernels(prof, steps):
-    return {k: {"ms_per_step": v[0] / steps, "gflop_per_step": v[1] / steps, "launches_per_step": v[2] / steps}
-            for k, v in sorted(prof.items(), key=lambda x: -x[1][0])}
-
-
-def _mixed_errors(plain, mixed, state):
-    """One pass of both forms from the same state; relative max-norm of the chosen form per quantity."""
+def _one_pass(sess, G, mu, stream):
+    """One pass by direct calls (P0, W, Sigma~, HF, Dyson with the mu search, energy) from a state."""
     import torch
 
-    G, Sig, Shf, mu = state
-
-    def run(sess):
+    with torch.cuda.stream(stream):
         P0 = sess.polarization(G)
         P = sess.screened(P0)
         S = sess.self_energy(G, P)
         H = sess.hartree_fock(G)
         Gn, mun = sess.dyson(S, H, mu, True)
-        E = sess.energy(Gn, H, S)
-        return dict(P0=P0, P=P, Sigma=S, HF=H, G=Gn), mun, E
+    E = sess.energy(Gn, H, S)
+    return dict(P0=P0, P=P, Sigma=S, HF=H, G=Gn), mun, E
 
-    a, mua, Ea = run(plain)
-    b, mub, Eb = run(mixed)
+
+def _second_form(other, head_sess, state, dev, flush):
+    """One pass of the other form from the head form's state, timed (CUDA events, per-kernel events on),
+    and the head form's error per quantity against it."""
+    import torch
+
+    from paper_2405_09494_gb300 import sgw
+
+    G, _, _, mu = state
+    stream = torch.cuda.Stream(dev)
+    flush.zero_()
+    torch.cuda.synchronize(dev)
+    sgw.sgw_profile_read(other.ctx, reset=True)
+    sgw.sgw_profile_enable(other.ctx, True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ra, mua, Ea = _one_pass(other, G, mu, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    t = a.elapsed_time(b) * 1e-3
+    prof = sgw.sgw_profile_read(other.ctx, reset=True)
+    sgw.sgw_profile_enable(other.ctx, False)
+    rb, mub, Eb = _one_pass(head_sess, G, mu, stream)
+    torch.cuda.synchronize(dev)
 
     def rel(x, y):
         return float((x - y).abs().max() / y.abs().max())
 
-    out = {k: rel(b[k], a[k]) for k in a}
-    out["mu"] = abs(mub - mua)
-    out["E"] = abs(Eb[0] - Ea[0]) / max(1.0, abs(Ea[0]))
-    torch.cuda.synchronize()
+    errs = {k: rel(rb[k], ra[k]) for k in ra}
+    errs["mu"] = abs(mub - mua)
+    errs["E"] = abs(Eb[0] - Ea[0]) / max(1.0, abs(Ea[0]))
+    return t, prof, errs
+
+
+def _roofline(prof, cfg, npairs, steps, step_s):
+    """Roofline of the kernel class with the most device time.
+
+    Tensor-core chains (chosen form): against the TF32 tensor peak / 3 (three TF32 products per
+    FP32-accurate product), the sustained figure when the pass lasts over a second; FP64 and FP32
+    kernels against their FMA pipes (derived: units per SM x SMs x clock)."""
+    hbm, bf16, bf16_sus, which = measured_peaks()
+    compute = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(compute, key=lambda k: compute[k][0])
+    ms, gf, nl = compute[dom]
+    achieved = (gf / nl) / (ms / nl)  # GFLOP per launch / ms per launch = TFLOP/s
+    out = {"kernel": dom, "achieved": achieved, "unit": "TFLOP/s", "traffic": None}
+    if dom.endswith("_tc"):
+        sustained = step_s > 1.0
+        peak = (bf16_sus if sustained else bf16) * 1.1 / 2.25 / 3
+        out.update(bound="tensor", peak=peak, peak_note=(
+            f"TF32 x3: bf16 {'sustained' if sustained else 'burst'} {bf16_sus if sustained else bf16:.1f} TF/s "
+            f"({which}) x nominal TF32/BF16 1.1/2.25, / 3 products"))
+        # the survey's minimum traffic of the chain kernels: V read once per launch (complex64)
+        vbytes = 8.0 * npairs * cfg.naux * cfg.nao * cfg.nao
+        out["algorithmic_bytes_per_launch"] = vbytes
+        out["flop_per_algorithmic_byte"] = gf * 1e9 / nl / vbytes
+    elif dom.endswith("_f32"):
+        out.update(bound="alu", peak=FP32_PEAK_TFLOPS,
+                   peak_note="FP32 FMA pipe: 128 per clock per SM x 152 SMs x 2070 MHz (derived)")
+    else:
+        out.update(bound="alu", peak=FP64_PEAK_TFLOPS,
+                   peak_note="FP64 FMA pipe: 2 per clock per SM x 152 SMs x 2070 MHz (derived; a DFMA probe measured 1.20)")
+    out["frac"] = achieved / out["peak"]
     return out
+
+
+def _kernels(prof, steps):
+    return {k: {"ms_per_step": v[0] / steps, "gflop_per_step": v[1] / steps, "launches_per_step": v[2] / steps}
+            for k, v in sorted(prof.items(), key=lambda x: -x[1][0])}
 
 
 def run_ours(args, rank, world, local):
@@ -392,72 +470,70 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     cfg = configs.get(args.config)
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    head = forms[0]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # inputs: the seeded generator, its two-body averaging run on the device (input preparation, untimed)
     system = synth.System(cfg, device=dev)
-    res = {}
-    sess = {}
-    for f in forms:
-        prec = sgw.SGW_FP64 if f == "plain" else sgw.SGW_MIXED_FP32
-        sess[f] = api.Session(cfg, precision=prec, device=str(dev), system=system)
-        res[f] = _time_form(sess[f], cfg, args, dev, local, flush, world, e2e=(f == forms[0] and not args.no_e2e))
-    if len(forms) == 2:
-        errs = _mixed_errors(sess["plain"], sess["mixed"], res["plain"]["state"])
-    elif forms == ["mixed"] and args.check_errors:
-        ref = api.Session(cfg, precision=sgw.SGW_FP64, device=str(dev), system=system)
-        errs = _mixed_errors(ref, sess["mixed"], res["mixed"]["state"])
-        ref.close()
-    else:
-        errs = None
-    npairs = int(sess[forms[0]].layout.npairs)
-    for f in forms:
-        sess[f].close()
 
-    def summary(f):
-        r = res[f]
-        gf = sum(v[1] for v in r["prof"].values()) / args.steps
-        return gf, _roofline(r["prof"], cfg.name, cfg, npairs, args.steps, r["t_step"])
+    def session(form):
+        return api.Session(cfg, precision=sgw.SGW_FP64 if form == "plain" else sgw.SGW_MIXED_FP32,
+                           device=str(dev), system=system)
 
-    head = forms[0]
-    gf_h, roof_h = summary(head)
-    rh = res[head]
+    sess = session(head)
+    res = _time_form(sess, cfg, args, dev, local, flush, world, e2e=not args.no_e2e)
+    npairs = int(sess.layout.npairs)
+    second = None
+    if len(forms) > 1 and not args.no_errors:
+        other = session(forms[1])
+        t2, prof2, errs = _second_form(other, sess, res["state"], dev, flush)
+        other.close()
+        second = dict(form=forms[1], t=t2, prof=prof2, errs=errs)
+    sess.close()
+
+    gf = sum(v[1] for v in res["prof"].values()) / args.steps
+    chosen = head != "plain"
     line = {
-        "metric": METRIC, "value": rh["t_step"], "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": rh["t_step"] * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if head == "plain" else "c64 chains, c128 rest",
+        "metric": METRIC, "value": res["t_step"], "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": res["t_step"] * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32x3 chains with fp32 accumulation, f64 rest" if chosen else "c128",
         "data": "synthetic",
         "config": {"workload": cfg.description, "name": cfg.name,
-                   "form": "plain (complex128)" if head == "plain" else "chosen (mixed)",
-                   "l2": "512 MiB buffer written between timed steps",
+                   "form": "chosen (mixed precision)" if chosen else "plain (complex128)",
+                   "why_not_c5": NOT_C5 if cfg.name != "c5" else None,
+                   "l2": "operands of several GB per pass (above L2) and a 512 MiB buffer written between timed steps",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "tflops_algorithmic": gf_h / rh["t_step"] / 1e3,
-        "step_times_s": rh["times"],
+        "tflops_algorithmic": gf / res["t_step"] / 1e3,
+        "step_times_s": res["times"],
         "cuda_graph": "each timed step replays one captured graph of the whole pass",
-        "gflop_per_step": gf_h,
-        "roofline": roof_h,
-        "kernels": _kernels(rh["prof"], args.steps),
-        "gpu_launches": int(sum(v[2] for v in rh["prof"].values())),
-        "clocks": rh["clocks"],
+        "gflop_per_step": gf,
+        "roofline": _roofline(res["prof"], cfg, npairs, args.steps, res["t_step"]),
+        "kernels": _kernels(res["prof"], args.steps),
+        "gpu_launches": int(sum(v[2] for v in res["prof"].values())),
+        "clocks": res["clocks"],
     }
-    if "e2e" in rh:
-        line["e2e"] = rh["e2e"]
-    if head == "mixed" and errs is not None:
-        line["error_vs_fp64"] = errs
-    if "mixed" in forms and head != "mixed":
-        rm = res["mixed"]
-        gf_m, roof_m = summary("mixed")
-        line["chosen_form"] = {
-            "form": "V-G-V and V-G-P-V chains complex64 with FP32 accumulation; W solve, Dyson, mu, transforms FP64",
-            "value": rm["t_step"], "unit": "s/iteration", "speedup_vs_plain": rh["t_step"] / rm["t_step"],
-            "tflops_algorithmic": gf_m / rm["t_step"] / 1e3, "roofline": roof_m,
-            "error_vs_fp64": errs, "kernels": _kernels(rm["prof"], args.steps), "clocks": rm["clocks"],
-            "gpu_launches": int(sum(v[2] for v in rm["prof"].values())),
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if second is not None:
+        gf2 = sum(v[1] for v in second["prof"].values())
+        line["error_vs_fp64" if chosen else "error_of_chosen_vs_this"] = second["errs"]
+        line[f"{second['form']}_form"] = {
+            "value": second["t"], "unit": "s/iteration", "steps": 1, "warmup": 0,
+            "how": "one pass by direct calls from the headline form's state (CUDA events, per-kernel events on); "
+                   "beside the headline, not a benchmark line",
+            "tflops_algorithmic": gf2 / second["t"] / 1e3, "gflop_per_step": gf2,
+            "speedup_of_chosen": (second["t"] / res["t_step"]) if chosen else (res["t_step"] / second["t"]),
+            "roofline": _roofline(second["prof"], cfg, npairs, 1, second["t"]),
+            "kernels": _kernels(second["prof"], 1),
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val, cores = oracle_sample(cfg)
-        line["cpu_baseline"] = {"value": val, "unit": "s/iteration", "cores": cores, "kind": "oracle",
-                                "sample": f"P0 + W at 1 of {cfg.nkpts} q and Sigma at 1 of {cfg.nkpts} k, scaled "
-                                          f"by {cfg.nkpts}; HF and Dyson with mu search in full"}
+        val, desc = oracle_sample(cfg, system)
+        line["cpu_baseline"] = {"value": val, "unit": "s/iteration", "cores": blas_threads(), "kind": "oracle",
+                                "sample": desc}
+        c1 = single_core_c1()
+        if c1 is not None:
+            line["cpu_baseline_c1_single_core"] = {"value": c1, "unit": "s/iteration", "cores": 1, "kind": "oracle",
+                                                   "sample": "one whole oracle pass of workload c1 from G0"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -465,14 +541,15 @@ def run_ours(args, rank, world, local):
 def main():
     args = _args()
     rank, world, local = _dist()
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks exit without work
+        run_reference(args, rank, world)
+        return
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-    else:
-        run_ours(args, rank, world, local)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local)
     if world > 1:
         import torch.distributed as dist
 

@@ -282,11 +282,12 @@ def density_matrix(G):
     return -np.einsum("t,ktij->kij", r, G)
 
 
-def hartree_fock(gamma, V, nk, s=2):
+def hartree_fock(gamma, V, nk, s=2, ks=None):
     """Sigma^(HF) = J + K of Eq. (sigma_hf).
 
     J^k_ij = (s/N_k) sum_{k'} sum_Q V^{kk}_ij(Q) sum_ab gamma^{k'}_ab V^{k'k'}_ba(Q)
     K^k_ij = -(1/N_k) sum_{k'} sum_Q sum_ab V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q)
+    ``ks`` restricts J and K to a list of k (other entries stay zero).
     """
     Vf = as_vfun(V)
     Nk = gamma.shape[0]
@@ -294,9 +295,9 @@ def hartree_fock(gamma, V, nk, s=2):
     rho = np.zeros(naux, dtype=np.complex128)
     for kp in range(Nk):
         rho += np.einsum("ab,Qba->Q", gamma[kp], Vf(kp, kp))
-    J = np.empty_like(gamma)
+    J = np.zeros_like(gamma)
     K = np.zeros_like(gamma)
-    for k in range(Nk):
+    for k in (range(Nk) if ks is None else ks):
         J[k] = (s / Nk) * np.einsum("Qij,Q->ij", Vf(k, k), rho)
         for kp in range(Nk):
             K[k] -= (1.0 / Nk) * np.einsum("Qia,ab,Qbj->ij", Vf(k, kp), gamma[kp], Vf(kp, k), optimize=True)

@@ -110,6 +110,13 @@ CONFIGS = {
         damping=0.5,
         description="rocksalt Oh, 4x4x4 mesh (8 wedge points), nao 104, naux 600, 200 tau, beta 500, "
                     "self-consistent loop with damping 0.5"),
+    # c3's cell and shells (nao 52, naux 300: the same tiles and blocks per pair) on a 2x2x2 mesh with
+    # 16 tau: a case small enough for full profiler captures of the c3/c4 kernels (operands of a few GB)
+    "c3s": Config(
+        name="c3s", index=12, structure="rocksalt", nk=(2, 2, 2), ao_shells=_shells({0: 4, 1: 4, 2: 2}),
+        aux_shells=_shells({0: 10, 1: 10, 2: 11, 3: 4, 4: 3}), ntau=16, beta=10.0, mats_f=F16, mats_b=B16,
+        damping=0.5,
+        description="rocksalt Oh, 2x2x2 mesh, nao 52, naux 300, 16 tau, beta 10 (profiling case of c3's kernels)"),
     # small rocksalt cell for the smoke run and the fast parity tests: 2x2x2 mesh (3 wedge points)
     "t1": Config(
         name="t1", index=10, structure="rocksalt", nk=(2, 2, 2), ao_shells=(0, 1), aux_shells=(0, 0, 1, 2),

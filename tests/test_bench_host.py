@@ -1,5 +1,7 @@
-"""Host logic of bench.py (no GPU): which roofline bound a kernel class is reported against."""
+"""Host logic of bench.py (no GPU): the roofline a kernel class is reported against, the measured
+peaks, the oracle's core count and which workloads get a whole oracle pass."""
 import importlib.util
+import json
 import os
 
 import pytest
@@ -19,38 +21,41 @@ def test_fp64_class_is_alu_bound(bench):
     from paper_2405_09494_gb300 import configs
 
     prof = {"sigma_pvg": (211.5, 257.1, 5), "p0_gram": (132.4, 125.9, 5), "gram_reduce": (1.0, 0.0, 20)}
-    r = bench._roofline(prof, "c2", configs.get("c2"), 108, 5, 0.104)
+    r = bench._roofline(prof, configs.get("c2"), 108, 5, 0.104)
     assert r["bound"] == "alu" and r["kernel"] == "sigma_pvg" and r["unit"] == "TFLOP/s"
     assert r["peak"] == pytest.approx(bench.FP64_PEAK_TFLOPS)
     assert r["frac"] == pytest.approx((257.1 / 211.5) / bench.FP64_PEAK_TFLOPS)
-    assert r["traffic"] == bench.DRAM_TRAFFIC_BYTES[("c2", "sigma_pvg")]
 
 
-def test_tensor_class_below_balance_point_is_hbm_bound(bench):
-    from paper_2405_09494_gb300 import configs
-
-    cfg = configs.get("c2")
-    # 51.4 GFLOP per launch over 2 x 108 x 50 x 100 x 18^2 x 8 bytes: about 18 flop per byte
-    prof = {"sigma_pvg_tc": (1.18, 51.42, 1), "p0_gram_tc": (0.9, 25.2, 1)}
-    r = bench._roofline(prof, "c2", cfg, 108, 1, 0.0097)
-    nbytes = 2.0 * 108 * cfg.ntau * cfg.naux * cfg.nao ** 2 * 8
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["achieved"] == pytest.approx(nbytes / 1.18e-3 / 1e9)
-    assert r["frac"] == pytest.approx(r["achieved"] / bench.HBM_PEAK_GBS)
-    assert r["flop_per_byte"] < bench.TF32_X3_PEAK_TFLOPS * 1e3 / bench.HBM_PEAK_GBS
-
-
-def test_tensor_class_above_balance_point_uses_the_sustained_peak_in_long_steps(bench):
+def test_tensor_class_is_tensor_bound_with_the_sustained_peak_in_long_steps(bench):
     from paper_2405_09494_gb300 import configs
 
     cfg = configs.get("c3")
-    prof = {"sigma_pvg_tc": (427.6, 40240.2, 50)}
-    long_step = bench._roofline(prof, "c3", cfg, 512, 1, 1.77)
-    short_step = bench._roofline(prof, "c3", cfg, 512, 1, 0.5)
+    prof = {"sigma_pvg_tc": (427.6, 40240.2, 50), "w_solve": (5.0, 1.0, 50)}
+    long_step = bench._roofline(prof, cfg, 512, 1, 1.77)
+    short_step = bench._roofline(prof, cfg, 512, 1, 0.5)
     assert long_step["bound"] == short_step["bound"] == "tensor"
-    assert long_step["peak"] == pytest.approx(bench.TF32_X3_SUSTAINED_TFLOPS)
-    assert short_step["peak"] == pytest.approx(bench.TF32_X3_PEAK_TFLOPS)
-    assert long_step["frac"] > short_step["frac"]
+    _, bf16, bf16_sus, _ = bench.measured_peaks()
+    assert long_step["peak"] == pytest.approx(bf16_sus * 1.1 / 2.25 / 3)
+    assert short_step["peak"] == pytest.approx(bf16 * 1.1 / 2.25 / 3)
+    assert long_step["frac"] >= short_step["frac"]
+    # the survey's minimum bytes of a chain launch: V once, complex64
+    assert long_step["algorithmic_bytes_per_launch"] == pytest.approx(8.0 * 512 * 300 * 52 * 52)
+
+
+def test_measured_peaks_are_read_from_the_file_or_fall_back(bench, tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, 1900.0, 1700.0, "of fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(
+        {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1600.0}))
+    assert bench.measured_peaks() == (6000.0, 1800.0, 1600.0, "of measured")
+
+
+def test_whole_oracle_pass_only_where_it_fits(bench):
+    from paper_2405_09494_gb300 import configs
+
+    assert bench.full_pass_fits(configs.get("c1")) and bench.full_pass_fits(configs.get("c2"))
+    assert not any(bench.full_pass_fits(configs.get(n)) for n in ("c3", "c4", "c5"))
 
 
 def test_oracle_core_count_follows_the_blas_thread_variables(bench, monkeypatch):
