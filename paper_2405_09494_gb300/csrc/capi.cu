@@ -32,12 +32,6 @@ void dfree(T*& p) {
 
 inline cudaStream_t S(sgw_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-size_t workspace_budget() {
-  const char* e = std::getenv("SGW_WORKSPACE_GB");
-  double gb = e ? std::atof(e) : 24.0;
-  if (gb < 0.5) gb = 0.5;
-  return (size_t)(gb * (1ull << 30));
-}
 
 double2 z(double re, double im = 0.0) { return make_double2(re, im); }
 
@@ -50,6 +44,22 @@ void free_plan(ContractionPlan& p) {
 }
 
 }  // namespace
+
+// Device memory the contraction plans may size their intermediates for: SGW_WORKSPACE_GB when set,
+// otherwise 64 GiB or half of the device memory free when the plan is built, whichever is less (the
+// tau chunk of the chains grows with it: V is then read from memory once per chunk).
+size_t sgw::workspace_budget() {
+  const char* e = std::getenv("SGW_WORKSPACE_GB");
+  double gb = 64.0;
+  if (e) {
+    gb = std::atof(e);
+  } else {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) gb = std::min(gb, 0.5 * (double)free_b / (1ull << 30));
+  }
+  if (gb < 0.5) gb = 0.5;
+  return (size_t)(gb * (1ull << 30));
+}
 
 namespace sgw {
 // single-precision copies of the tau series used by the chosen form (kept apart from the workspace)

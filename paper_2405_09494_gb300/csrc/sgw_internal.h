@@ -329,6 +329,7 @@ inline void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
 }
 
 sgw_status lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st);
+size_t workspace_budget();  // bytes the contraction plans may size their intermediates for
 double gram_elems(const sgw_ctx* c, int nb);  // elements a Gram stage contracts in a block of nb
 
 // tensor-core chains of the chosen form (tc.cu)

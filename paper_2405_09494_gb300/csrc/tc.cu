@@ -919,9 +919,7 @@ int qindex(const sgw_ctx* c, int k1, int k2) {
 
 long long tc_nc(const sgw_ctx* c, long long np) {
   const long long vs = (long long)c->naux * c->nao * c->nao;
-  const char* s = std::getenv("SGW_WORKSPACE_GB");
-  const double gb = s ? std::atof(s) : 24.0;
-  const double budget = gb * 1e9;
+  const double budget = (double)workspace_budget();
   long long nc = (long long)(budget * 0.6 / (2.0 * np * vs * sizeof(float2)));
   nc = std::max(1LL, std::min<long long>({nc, (long long)c->nt, 128LL}));
   const long long nchunks = (c->nt + nc - 1) / nc;
@@ -1042,26 +1040,43 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   std::vector<TcJob> vg, gvg;
   T.vg_start.assign(nt + 1, 0); T.gvg_start.assign(nt + 1, 0);
   const int nch_o = (2 * nao + 15) / 16;
-  for (int t = 0; t < nt; ++t) {
-    const int tl = t % nc;
-    T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size();
+  // V G jobs of a tau chunk in the order [pair][column tile][tau]: the nc units that read the same
+  // V tile for the chunk's tau values run side by side, so V comes from memory once per chunk and
+  // from L2 for the other tau values.  G(-tau) Z' jobs read a Z' tile per tau and keep tau order.
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long first = (long long)vg.size();
+    for (int t = t0; t < t1; ++t) T.vg_start[t] = first;
     for (long long lp = 0; lp < np; ++lp)
-      for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
-        const long long p = T.pb + lp;
-        const int k1 = c->pair_k1[0][p], k2 = c->pair_k2[0][p];
-        TcJob j{};
-        j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
-        j.b_z = (int)(((long long)0 * nt + t) * nw + c->rep[k2]);
-        j.a_x = 0; j.b_x = 0; j.nslab = 1; j.nchunk = nch_o; j.a_dz = 0; j.b_dz = 0;
-        j.m_rows = rows; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
-        j.out_off = ((long long)tl * np + lp) * rows * nao + (long long)n0 * nao;  // Z'[A][j][c], column j = n0 + n
-        vg.push_back(j);
-        TcJob g = j;
-        g.a_z = (int)((long long)tl * np + lp);
-        g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
-        g.out_off = lp * nc * (long long)rows * nao + (long long)tl * nao * nao + (long long)n0 * nao;  // X[p][Q][tl][i][j]
-        gvg.push_back(g);
-      }
+      for (int n0 = 0; n0 < nao; n0 += 64)  // output columns in tiles of 64
+        for (int t = t0; t < t1; ++t) {
+          const int tl = t - t0;
+          const long long p = T.pb + lp;
+          const int k2 = c->pair_k2[0][p];
+          TcJob j{};
+          j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
+          j.b_z = (int)(((long long)0 * nt + t) * nw + c->rep[k2]);
+          j.a_x = 0; j.b_x = 0; j.nslab = 1; j.nchunk = nch_o; j.a_dz = 0; j.b_dz = 0;
+          j.m_rows = rows; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
+          j.out_off = ((long long)tl * np + lp) * rows * nao + (long long)n0 * nao;  // Z'[A][j][c], column j = n0 + n
+          vg.push_back(j);
+        }
+    for (int t = t0; t < t1; ++t) {
+      const int tl = t - t0;
+      T.gvg_start[t] = gvg.size();
+      for (long long lp = 0; lp < np; ++lp)
+        for (int n0 = 0; n0 < nao; n0 += 64) {
+          const long long p = T.pb + lp;
+          const int k1 = c->pair_k1[0][p];
+          TcJob g{};
+          g.a_y = 0; g.a_z = (int)((long long)tl * np + lp); g.b_y = n0;
+          g.b_z = (int)(((long long)1 * nt + (nt - 1 - t)) * nw + c->rep[k1]);
+          g.a_x = 0; g.b_x = 0; g.nslab = 1; g.nchunk = nch_o; g.a_dz = 0; g.b_dz = 0;
+          g.m_rows = rows; g.n_valid = std::min(64, nao - n0); g.n_mma = round16(g.n_valid);
+          g.out_off = lp * nc * (long long)rows * nao + (long long)tl * nao * nao + (long long)n0 * nao;  // X[p][Q][tl][i][j]
+          gvg.push_back(g);
+        }
+    }
   }
   T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size();
   T.unit_p0 = unit_override() ? unit_override() : kUnitDefault;
@@ -1165,34 +1180,46 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
   std::vector<TcJob> svg, pvg;
   T.svg_start.assign(nt + 1, 0); T.pvg_start.assign(nt + 1, 0);
   const int nch_o = (2 * nao + 15) / 16;
-  for (int t = 0; t < nt; ++t) {
-    const int tl = t % nc;
-    T.svg_start[t] = svg.size(); T.pvg_start[t] = pvg.size();
-    for (long long lp = 0; lp < np; ++lp) {
-      const long long p = T.pb + lp;
-      const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
-      for (int n0 = 0; n0 < nao; n0 += 64) {  // output columns in tiles of 64
-        TcJob j{};
-        j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
-        j.b_z = (int)((long long)t * nw + c->rep[k2]);
-        j.nslab = 1; j.nchunk = nch_o;
-        j.m_rows = rows_v; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
-        j.out_off = ((long long)tl * np + lp) * vs + (long long)n0 * naux;  // X1T[i][b][A], column b = n0 + n
-        svg.push_back(j);
-      }
-      const int wq = c->rep[qindex(c, k1, k2)];
-      for (int b : wblocks[wq]) {
-        const int s = info[3 * b], nb = info[3 * b + 1], d = info[3 * b + 2];
-        for (int n0 = 0; n0 < nb; n0 += 64) {
-          TcJob v{};
-          v.a_y = 0; v.a_z = (int)((long long)tl * np + lp);
-          v.a_x = 2 * s - d;
-          v.b_y = n0; v.b_z = tl * ninst + b;
-          v.b_x = 0;
-          v.nslab = 1; v.nchunk = (d + 2 * nb + 15) / 16;
-          v.m_rows = rows_x; v.n_valid = std::min(64, nb - n0); v.n_mma = round16(v.n_valid);
-          v.out_off = lp * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
-          pvg.push_back(v);
+  // Vt G jobs in the order [pair][column tile][tau] within a tau chunk (Vt read once per chunk, as
+  // for P0); P^T X1 jobs read an X1 tile per tau and keep tau order
+  for (int t0 = 0; t0 < nt; t0 += nc) {
+    const int t1 = std::min(nt, t0 + nc);
+    const long long first = (long long)svg.size();
+    for (int t = t0; t < t1; ++t) T.svg_start[t] = first;
+    for (long long lp = 0; lp < np; ++lp)
+      for (int n0 = 0; n0 < nao; n0 += 64)  // output columns in tiles of 64
+        for (int t = t0; t < t1; ++t) {
+          const int tl = t - t0;
+          const long long p = T.pb + lp;
+          const int k2 = c->pair_k2[1][p];
+          TcJob j{};
+          j.a_y = 0; j.a_z = (int)p; j.b_y = n0;
+          j.b_z = (int)((long long)t * nw + c->rep[k2]);
+          j.nslab = 1; j.nchunk = nch_o;
+          j.m_rows = rows_v; j.n_valid = std::min(64, nao - n0); j.n_mma = round16(j.n_valid);
+          j.out_off = ((long long)tl * np + lp) * vs + (long long)n0 * naux;  // X1T[i][b][A], column b = n0 + n
+          svg.push_back(j);
+        }
+    for (int t = t0; t < t1; ++t) {
+      const int tl = t - t0;
+      T.pvg_start[t] = pvg.size();
+      for (long long lp = 0; lp < np; ++lp) {
+        const long long p = T.pb + lp;
+        const int k1 = c->pair_k1[1][p], k2 = c->pair_k2[1][p];
+        const int wq = c->rep[qindex(c, k1, k2)];
+        for (int b : wblocks[wq]) {
+          const int s = info[3 * b], nb = info[3 * b + 1], d = info[3 * b + 2];
+          for (int n0 = 0; n0 < nb; n0 += 64) {
+            TcJob v{};
+            v.a_y = 0; v.a_z = (int)((long long)tl * np + lp);
+            v.a_x = 2 * s - d;
+            v.b_y = n0; v.b_z = tl * ninst + b;
+            v.b_x = 0;
+            v.nslab = 1; v.nchunk = (d + 2 * nb + 15) / 16;
+            v.m_rows = rows_x; v.n_valid = std::min(64, nb - n0); v.n_mma = round16(v.n_valid);
+            v.out_off = lp * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
+            pvg.push_back(v);
+          }
         }
       }
     }
