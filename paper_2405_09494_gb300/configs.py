@@ -108,6 +108,9 @@ CONFIGS = {
         name="c5", index=4, structure="rocksalt", nk=(4, 4, 4), ao_shells=_shells({0: 7, 1: 6, 2: 4, 3: 1}),
         aux_shells=_shells({0: 20, 1: 20, 2: 22, 3: 8, 4: 6}), ntau=200, beta=500.0, mats_f=F200, mats_b=B200,
         damping=0.5,
+        # couplings scaled by 0.5: at unit scale the exchange term of its 52 occupied orbitals moves
+        # Sigma by 20.7 Ha in the first pass and the mu root out of the search bracket [-20, 20]
+        extra={"vscale": 0.5},
         description="rocksalt Oh, 4x4x4 mesh (8 wedge points), nao 104, naux 600, 200 tau, beta 500, "
                     "self-consistent loop with damping 0.5"),
     # c3's cell and shells (nao 52, naux 300: the same tiles and blocks per pair) on a 2x2x2 mesh with

@@ -74,6 +74,8 @@ struct TcPlan {
   long long unit_p0 = 0, unit_s = 0;   // split-K unit length of the Gram reductions (chunks)
   bool tuned_p0 = false, tuned_s = false;
   int nc_p0 = 0, nc_s = 0;
+  int nc_req_p0 = 0, nc_req_s = 0;         // tau chunk asked for (0: the largest the workspace allows)
+  bool tuned_nc_p0 = false, tuned_nc_s = false;
   std::vector<long long> vg_start, gvg_start, pg_start, pr_start;            // per tau: first job / unit / tile
   std::vector<long long> svg_start, pvg_start, sg_start, sr_start;
   TcJob *d_vg = nullptr, *d_gvg = nullptr, *d_pg = nullptr, *d_svg = nullptr, *d_pvg = nullptr, *d_sg = nullptr;
@@ -917,6 +919,17 @@ int qindex(const sgw_ctx* c, int k1, int k2) {
   return (a * n2 + b) * n3 + cc;
 }
 
+// tau values per chunk for at most n per chunk, the chunks balanced over the ntau values
+long long balanced_nc(long long nt, long long n) {
+  n = std::max(1LL, std::min(n, nt));
+  const long long nchunks = (nt + n - 1) / n;
+  return (nt + nchunks - 1) / nchunks;
+}
+long long nc_override() {
+  const char* s = std::getenv("SGW_TC_NC");
+  return s ? std::max(1LL, std::atoll(s)) : 0;
+}
+
 long long tc_nc(const sgw_ctx* c, long long np) {
   const long long vs = (long long)c->naux * c->nao * c->nao;
   const double budget = (double)workspace_budget();
@@ -1033,7 +1046,7 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   CKS(tables_common(c, T));
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
   const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
-  const int nc = (int)tc_nc(c, np);
+  const int nc = T.nc_req_p0 > 0 ? (int)balanced_nc(nt, T.nc_req_p0) : (int)tc_nc(c, np);
   T.nc_p0 = nc;
   const int rows = naux * nao;
   T.mt_vg = (rows + 127) / 128;
@@ -1151,7 +1164,7 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
   CKS(tables_common(c, T));
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
   const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
-  const int nc = (int)tc_nc(c, np);
+  const int nc = T.nc_req_s > 0 ? (int)balanced_nc(nt, T.nc_req_s) : (int)tc_nc(c, np);
   T.nc_s = nc;
   T.slot_s = kSlotD;
   const long long vs = (long long)naux * nao * nao;
@@ -1301,15 +1314,15 @@ static sgw_status tune_unit(sgw_ctx* c, cudaStream_t st, const char* what, long 
   return SGW_OK;
 }
 
-sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long pb, long long pe, cudaStream_t st) {
-  TcPlan& T = plan_for(c, pb, pe);
-  CKS(build_p0(c, T));
+// The P0 chain over the plan's tau chunks.  With trial_ms, only the first chunk runs, twice, and
+// the time of the second run (ms) is returned there (the tau-chunk autotuner).
+static sgw_status p0_run(sgw_ctx* c, TcPlan& T, const double2* G, double2* out, cudaStream_t st, float* trial_ms) {
   const int nt = c->nt, nw = c->nwedge, nao = c->nao, naux = c->naux, Nk = c->Nk, nc = T.nc_p0;
   // np: pairs of the range (intermediate slabs); npg: the whole pair list (V slabs)
   const long long np = T.pe - T.pb, npg = (long long)nw * Nk, vs = (long long)naux * nao * nao;
   const long long inter = (long long)nc * np * vs;  // complex64 elements
   const long long gop = 2LL * nt * nw * 4 * nao * 2 * nao;  // floats
-  const bool tune = !T.tuned_p0 && autotune_enabled() && !capturing(st);
+  const bool tune = !T.tuned_p0 && autotune_enabled() && !capturing(st) && !trial_ms;
   long long max_units = T.max_units_p0;
   if (tune) {  // partial tiles for the candidate with the most units
     for (long long cand : kUnitCandidates) {
@@ -1340,7 +1353,13 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long
   CKS(make_map(c, &mXg, X, 2LL * nao * nao, (long long)naux * nc, np, 8LL * nao * nao, (long long)nc * vs * 8, 32));
   CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, npg, 8LL * nao * nao, vs * 8, 64));
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
+  const int t_end = trial_ms ? std::min(nt, nc) : nt, reps = trial_ms ? 2 : 1;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (trial_ms && (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess))
+    return c->fail(SGW_ERR_CUDA, "autotuner events");
+  for (int rep = 0; rep < reps; ++rep) {
+  if (trial_ms && rep == reps - 1) cudaEventRecord(ea, st);
+  for (int t0 = 0; t0 < t_end; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     TcArgs a{};
     a.a_box = 128;
@@ -1387,20 +1406,84 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long
     CKS(s3);
     run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
+  }
+  if (trial_ms) {
+    cudaEventRecord(eb, st);
+    const bool ok = cudaEventSynchronize(eb) == cudaSuccess && cudaEventElapsedTime(trial_ms, ea, eb) == cudaSuccess;
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    return ok ? SGW_OK : c->fail(SGW_ERR_CUDA, "autotuner timing");
+  }
   if (tune) T.tuned_p0 = true;
   return lower_from_upper(c, 1, out, st);
 }
 
-sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, long long pb, long long pe,
-                          cudaStream_t st) {
+// Candidate tau chunks of the autotuner: the largest the workspace allows, about half and about a
+// quarter of it (distinct, balanced over the tau values), largest first.
+static std::vector<int> nc_candidates(long long nt, long long ncmax) {
+  std::vector<int> out;
+  for (long long d : {1LL, 2LL, 4LL}) {
+    const int v = (int)balanced_nc(nt, (ncmax + d - 1) / d);
+    if (std::find(out.begin(), out.end(), v) == out.end()) out.push_back(v);
+  }
+  return out;
+}
+
+// Tau-chunk autotuner: the chunk sets the shape of the Gram tiles (128 rows = 128 / nc auxiliary
+// rows x nc tau values against the same V rows), how often V is read and the number of launches.
+// On a context's first call outside a stream capture each candidate is built and the first chunk
+// of the chain timed (second of two runs); the fastest per tau value is kept.  SGW_TC_NC fixes it.
+template <class Build, class Run>
+static sgw_status tune_nc(sgw_ctx* c, long long nt, long long ncmax, int& req, bool& built, const char* what,
+                          Build&& build, Run&& runone) {
+  const std::vector<int> cands = nc_candidates(nt, ncmax);
+  if (cands.size() < 2) return SGW_OK;
+  float best = 1e30f;
+  int best_nc = cands[0];
+  for (int cand : cands) {
+    req = cand;
+    built = false;
+    CKS(build());
+    float ms = 0.f;
+    CKS(runone(&ms));
+    if (ms / cand < best) {
+      best = ms / cand;
+      best_nc = cand;
+    }
+  }
+  req = best_nc;
+  built = false;
+  const char* v = std::getenv("SGW_VERBOSE");
+  if (v && v[0] == '1')
+    std::fprintf(stderr, "sgw autotune: %s tau chunk %d (%.4f ms per tau value)\n", what, best_nc, best);
+  return SGW_OK;
+}
+
+sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long pb, long long pe, cudaStream_t st) {
   TcPlan& T = plan_for(c, pb, pe);
-  CKS(build_sigma(c, T));
+  if (!T.tuned_nc_p0) {
+    if (nc_override()) {
+      T.nc_req_p0 = (int)nc_override();
+      T.built_p0 = false;
+      T.tuned_nc_p0 = true;
+    } else if (autotune_enabled() && !capturing(st)) {
+      CKS(tune_nc(c, c->nt, tc_nc(c, T.pe - T.pb), T.nc_req_p0, T.built_p0, "P0", [&] { return build_p0(c, T); },
+                  [&](float* ms) { return p0_run(c, T, G, out, st, ms); }));
+      T.tuned_nc_p0 = true;
+    }
+  }
+  CKS(build_p0(c, T));
+  return p0_run(c, T, G, out, st, nullptr);
+}
+
+static sgw_status s_run(sgw_ctx* c, TcPlan& T, const double2* G, const double2* P, double2* out, cudaStream_t st,
+                        float* trial_ms) {
   const int nt = c->nt, nw = c->nwedge, nao = c->nao, naux = c->naux, Nk = c->Nk, nc = T.nc_s;
   const long long np = T.pe - T.pb, npg = (long long)nw * Nk, vs = (long long)naux * nao * nao;
   const long long inter = (long long)nc * np * vs;
   const long long gop = 1LL * nt * nw * 4 * nao * 2 * nao;
   const long long pop = (long long)nc * T.ninst * 4 * T.pt_rows * T.pt_k;
-  const bool tune = !T.tuned_s && autotune_enabled() && !capturing(st);
+  const bool tune = !T.tuned_s && autotune_enabled() && !capturing(st) && !trial_ms;
   long long max_units = T.max_units_s;
   if (tune) {  // partial tiles for the candidate with the most units
     for (long long cand : kUnitCandidates) {
@@ -1431,7 +1514,13 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
                 16LL * T.pt_k * T.pt_rows, 64));
   CKS(make_map(c, &mX2g, X2, 2LL * naux * nao, (long long)nao * nc, np, 8LL * naux * nao, (long long)nc * vs * 8, 32));
   CKS(make_map(c, &mVtg, c->d_V32[1], 2LL * naux * nao, nao, npg, 8LL * naux * nao, vs * 8, 64));
-  for (int t0 = 0; t0 < nt; t0 += nc) {
+  const int t_end = trial_ms ? std::min(nt, nc) : nt, reps = trial_ms ? 2 : 1;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (trial_ms && (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess))
+    return c->fail(SGW_ERR_CUDA, "autotuner events");
+  for (int rep = 0; rep < reps; ++rep) {
+  if (trial_ms && rep == reps - 1) cudaEventRecord(ea, st);
+  for (int t0 = 0; t0 < t_end; t0 += nc) {
     const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
     run(c, "tc_prep", 0.0, 1, st, [&] {
       k_tc_p_operands<<<gridn((long long)ntc * T.ninst * T.pt_rows * T.pt_k, 256), 256, 0, st>>>(
@@ -1485,8 +1574,34 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
     CKS(s3);
     run(c, "gram_reduce", 0.0, 1, st, reduce);
   }
+  }
+  if (trial_ms) {
+    cudaEventRecord(eb, st);
+    const bool ok = cudaEventSynchronize(eb) == cudaSuccess && cudaEventElapsedTime(trial_ms, ea, eb) == cudaSuccess;
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    return ok ? SGW_OK : c->fail(SGW_ERR_CUDA, "autotuner timing");
+  }
   if (tune) T.tuned_s = true;
   return lower_from_upper(c, 0, out, st);
+}
+
+sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double2* out, long long pb, long long pe,
+                          cudaStream_t st) {
+  TcPlan& T = plan_for(c, pb, pe);
+  if (!T.tuned_nc_s) {
+    if (nc_override()) {
+      T.nc_req_s = (int)nc_override();
+      T.built_sigma = false;
+      T.tuned_nc_s = true;
+    } else if (autotune_enabled() && !capturing(st)) {
+      CKS(tune_nc(c, c->nt, tc_nc(c, T.pe - T.pb), T.nc_req_s, T.built_sigma, "Sigma",
+                  [&] { return build_sigma(c, T); }, [&](float* ms) { return s_run(c, T, G, P, out, st, ms); }));
+      T.tuned_nc_s = true;
+    }
+  }
+  CKS(build_sigma(c, T));
+  return s_run(c, T, G, P, out, st, nullptr);
 }
 
 }  // namespace sgw

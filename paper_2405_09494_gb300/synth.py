@@ -377,11 +377,14 @@ class System:
             acc = np.zeros_like(X)
         n = 0
         for iop in range(len(self.ops)):
+            a, b = self.mesh.image[iop][p[0]], self.mesh.image[iop][p[1]]
             for swap in (0, 1):
+                # only the stabiliser of the pair contributes: skip the action of the other operations
+                if ((b, a) if swap else (a, b)) != p:
+                    continue
                 q, Y = self._act_pair(iop, swap, p[0], p[1], X)
-                if q == p:
-                    acc += Y
-                    n += 1
+                acc += Y
+                n += 1
         V = acc / n
         self._vcache[p] = V
         return V

@@ -5,6 +5,9 @@
   4 and one of 2).  P0 and Sigma~ must equal the single-chunk results of the default workspace:
   1e-12 in the plain form, 1e-6 in the chosen form (the split-K grouping of its FP32 partial
   tiles follows the chunking).
+* The chosen form with its tau chunk forced (SGW_TC_NC = 1, 3, 7: one tau value per Gram tile row
+  group, a ragged chunking, a prime one) against its autotuned default: 1e-6 (the tau chunk sets
+  the Gram tiles and the split-K grouping, so only the FP32 summation order changes).
 * A Gamma-only mesh (n_k = 1, no symmetry and rocksalt O_h): the whole chain against the oracle.
 """
 import dataclasses
@@ -54,6 +57,35 @@ def test_many_tau_chunks_equal_one_chunk(form, tol):
         os.environ.pop("SGW_WORKSPACE_GB", None)
     for a, b in zip(out, ref):
         assert rel_err(a, b) < tol, (form, rel_err(a, b))
+
+
+@pytest.fixture(scope="module")
+def c2_default_chain():
+    _need_gpu()
+    from paper_2405_09494_gb300 import api, configs, sgw, synth
+
+    cfg = configs.get("c2")
+    system = synth.System(cfg)
+    sess = api.Session(cfg, precision=sgw.SGW_MIXED_FP32, system=system)
+    ref = _chain(sess)
+    sess.close()
+    return cfg, system, ref
+
+
+@pytest.mark.parametrize("nc", ["1", "3", "7"])
+def test_forced_tau_chunks_of_the_chosen_form(c2_default_chain, nc):
+    from paper_2405_09494_gb300 import api, sgw
+
+    cfg, system, ref = c2_default_chain
+    os.environ["SGW_TC_NC"] = nc
+    try:
+        sess = api.Session(cfg, precision=sgw.SGW_MIXED_FP32, system=system)
+        out = _chain(sess)
+        sess.close()
+    finally:
+        os.environ.pop("SGW_TC_NC", None)
+    for a, b in zip(out, ref):
+        assert rel_err(a, b) < 1e-6, (nc, rel_err(a, b))
 
 
 @pytest.mark.parametrize("structure", ["none", "rocksalt"])
