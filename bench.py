@@ -47,6 +47,12 @@ DEFAULT_CONFIG = "c4"
 NOT_C5 = ("c5 (rocksalt, nao 104, naux 600, 200 tau) takes about a minute per chosen-form pass and tens of "
           "minutes per plain pass, beyond a benchmark run; its loop is recorded separately")
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz
+# DRAM bytes (read + write) per (pair, tau) unit of a kernel class, from one ncu capture of the same
+# kernel on the small case c3s (c3's tile sizes: nao 52, naux 300; profiles/k_tc_persist_c3s.md):
+# reported as the roofline's traffic, scaled by the units one launch processes, on workloads with
+# those tile sizes (c3, c4), while the kernel is unchanged.
+DRAM_BYTES_PER_UNIT = {"sigma_pvg_tc": (3.104321e9 + 2.457611e9) / (24 * 16)}
+TRAFFIC_SIZES = {"c3", "c4", "c3s"}
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 
 
@@ -436,6 +442,12 @@ def _roofline(prof, cfg, npairs, steps, step_s):
     ms, gf, nl = compute[dom]
     achieved = (gf / nl) / (ms / nl)  # GFLOP per launch / ms per launch = TFLOP/s
     out = {"kernel": dom, "achieved": achieved, "unit": "TFLOP/s", "traffic": None}
+    if dom in DRAM_BYTES_PER_UNIT and cfg.name in TRAFFIC_SIZES:
+        # units per launch: every pair at the launch's tau values (ntau / launches per pass)
+        tau_per_launch = cfg.ntau / (nl / steps)
+        out["traffic"] = DRAM_BYTES_PER_UNIT[dom] * npairs * tau_per_launch
+        out["traffic_note"] = ("ncu DRAM bytes per (pair, tau) unit on the small case c3s, scaled by the units of "
+                               "one launch")
     if dom.endswith("_tc"):
         sustained = step_s > 1.0
         peak = (bf16_sus if sustained else bf16) * 1.1 / 2.25 / 3

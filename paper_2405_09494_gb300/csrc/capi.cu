@@ -317,7 +317,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   cudaDeviceSynchronize();
   dfree(c->d_TF); dfree(c->d_TFbar); dfree(c->d_TB); dfree(c->d_TBbar);
   dfree(c->d_beta_row); dfree(c->d_gl_interp); dfree(c->d_nu_f); dfree(c->d_tau);
-  dfree(c->d_Uao); dfree(c->d_Uaux);
+  dfree(c->d_Uao); dfree(c->d_Uaux); dfree(c->d_refl); dfree(c->d_reflM);
   dfree(c->d_ao_start); dfree(c->d_ao_size); dfree(c->d_ao_doff);
   dfree(c->d_aux_start); dfree(c->d_aux_size); dfree(c->d_aux_doff);
   dfree(c->d_full_start); dfree(c->d_full_size); dfree(c->d_full_doff);
@@ -366,6 +366,100 @@ extern "C" SGW_API sgw_status sgw_sync(sgw_ctx* c, sgw_stream stream) {
 // ---------------------------------------------------------------------------
 // a1: irrep basis
 // ---------------------------------------------------------------------------
+// tau reflection of P0 (the survey's reading C-5; Algorithm 3 loops tau to n_tau/2).  From
+// Eq. (P0) with G(tau - beta) = -G(tau) and V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger,
+//     P0^q(tau) = P0^{-q}(beta - tau)^T   (auxiliary basis, every q, every tau).
+// On the Chebyshev roots beta - tau_j = tau_{n-1-j}.  In block coordinates, with U^k the rotated
+// auxiliary basis of point k (P0^k = U^k P0_blk^{rep(k)} U^k^dagger), the wedge point w of q and
+// the wedge point w' of -q:
+//     P0_blk^w(tau) = M P0_blk^{w'}(beta - tau)^T M^dagger,   M = U^q^dagger conj(U^{-q}).
+// M maps the blocks of w' onto those of w (both are irrep bases of the same little group); when it
+// does so block by block for every wedge point, only the first ceil(n_tau/2) tau values are
+// contracted and the rest follow from this relation.  SGW_P0_REFLECT=0 turns it off.
+static sgw_status setup_p0_reflection(sgw_ctx* c) {
+  c->refl_ok = false;
+  c->n_refl = 0;
+  dfree(c->d_refl);
+  dfree(c->d_reflM);
+  const char* e = std::getenv("SGW_P0_REFLECT");
+  if ((e && e[0] == '0') || c->nt < 2) return SGW_OK;
+  const int n = c->naux, n1 = c->p.nk[0], n2 = c->p.nk[1], n3 = c->p.nk[2];
+  const auto& U = c->hostU[1];  // [Nk][n][n], U[k][row][col]: column col is basis vector col
+  auto kneg = [&](int k) {
+    const int a = k / (n2 * n3), b = (k / n3) % n2, cc = k % n3;
+    return (((n1 - a) % n1) * n2 + ((n2 - b) % n2)) * n3 + ((n3 - cc) % n3);
+  };
+  std::vector<ReflItem> items;
+  std::vector<double2> Ms;
+  std::vector<cplx> M((size_t)n * n);
+  for (int w = 0; w < c->nwedge; ++w) {
+    const int q = c->wedge_k[w], mq = kneg(q), w2 = c->rep[mq];
+    const cplx* Uq = U.data() + (size_t)q * n * n;
+    const cplx* Um = U.data() + (size_t)mq * n * n;
+    // M[i][j] = sum_r conj(Uq[r][i]) conj(Um[r][j])
+    std::fill(M.begin(), M.end(), cplx(0, 0));
+    for (int r = 0; r < n; ++r)
+      for (int i = 0; i < n; ++i) {
+        const cplx a = std::conj(Uq[(size_t)r * n + i]);
+        if (a == cplx(0, 0)) continue;
+        const cplx* ur = Um + (size_t)r * n;
+        cplx* mr = M.data() + (size_t)i * n;
+        for (int j = 0; j < n; ++j) mr[j] += a * std::conj(ur[j]);
+      }
+    const Partition& Pt = c->part_aux[w];
+    const Partition& Ps = c->part_aux[w2];
+    std::vector<int> ss(Ps.sizes.size());
+    for (size_t b = 0, s0 = 0; b < Ps.sizes.size(); s0 += Ps.sizes[b], ++b) ss[b] = (int)s0;
+    int st = 0;
+    long long doff = 0;
+    for (int nb : Pt.sizes) {
+      // the source block holding this row block's weight; everything else must vanish
+      double best = -1.0, total = 0.0;
+      int bb = -1;
+      for (size_t b2 = 0; b2 < Ps.sizes.size(); ++b2) {
+        double f = 0.0;
+        for (int i = st; i < st + nb; ++i)
+          for (int j = ss[b2]; j < ss[b2] + Ps.sizes[b2]; ++j) f += std::norm(M[(size_t)i * n + j]);
+        total += f;
+        if (f > best) { best = f; bb = (int)b2; }
+      }
+      // off-block elements of M at most about 1e-10 (they are rounding of the bases): else no reflection
+      if (bb < 0 || Ps.sizes[bb] != nb || total - best > 1e-20 * (double)nb * n) return SGW_OK;
+      long long soff = 0;
+      for (int b2 = 0; b2 < bb; ++b2) soff += (long long)Ps.sizes[b2] * Ps.sizes[b2];
+      items.push_back({c->p_off[w] + doff, c->p_off[w2] + soff, (long long)Ms.size(), nb, 0});
+      for (int i = st; i < st + nb; ++i)
+        for (int j = ss[bb]; j < ss[bb] + nb; ++j) {
+          const cplx m = M[(size_t)i * n + j];
+          Ms.push_back(make_double2(m.real(), m.imag()));
+        }
+      st += nb;
+      doff += (long long)nb * nb;
+    }
+  }
+  CKS(upload(c, c->d_refl, items));
+  CKS(upload(c, c->d_reflM, Ms));
+  c->n_refl = (int)items.size();
+  c->refl_ok = true;
+  return SGW_OK;
+}
+
+int sgw::p0_tau_count(const sgw_ctx* c, long long pb, long long pe) {
+  const bool whole = pb == 0 && pe == (long long)c->nwedge * c->Nk;
+  return whole && c->refl_ok ? (c->nt + 1) / 2 : c->nt;
+}
+
+sgw_status sgw::p0_complete(sgw_ctx* c, double2* P0, int nt_eff, cudaStream_t st) {
+  CKS(lower_from_upper(c, 1, P0, st));
+  if (nt_eff >= c->nt) return SGW_OK;
+  const size_t need = (size_t)(c->nt - nt_eff) * c->p_elems;
+  CKS(ensure_workspace(c, need * sizeof(double2)));
+  run(c, "p0_reflect", 0.0, 1, st, [&] {
+    p0_reflect(c->d_refl, c->n_refl, P0, c->p_elems, c->nt, nt_eff, c->d_reflM, c->d_ws, st);
+  });
+  return lower_from_upper(c, 1, P0, st);  // exactly Hermitian blocks (the products are, up to rounding)
+}
+
 extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_structure* st, sgw_layout* out) {
   if (!c || !st || !out) return SGW_ERR_ARG;
   if (st->natom < 1 || st->nops < 1 || !st->positions || !st->rotations || !st->translations || !st->ao_shells ||
@@ -373,6 +467,7 @@ extern "C" SGW_API sgw_status sgw_build_irrep_basis(sgw_ctx* c, const sgw_struct
     return c->fail(SGW_ERR_ARG, "incomplete structure");
   CKS(build_symmetry(c, st));
   const int Nk = c->Nk, nao = c->nao, naux = c->naux, nw = c->nwedge;
+  CKS(setup_p0_reflection(c));
   for (int b = 0; b < 2; ++b) {
     std::vector<double2> t(c->hostU[b].size());
     for (size_t i = 0; i < t.size(); ++i) t[i] = make_double2(c->hostU[b][i].real(), c->hostU[b][i].imag());
@@ -766,14 +861,16 @@ static sgw_status build_p0_plan(sgw_ctx* c, ContractionPlan& P, long long pb, lo
   P.pb = pb;
   P.pe = pe;
   const int Nk = c->Nk, nt = c->nt, nao = c->nao;
+  const int nte = p0_tau_count(c, pb, pe);  // tau values contracted; the rest by the reflection
+  P.nt_eff = nte;
   const long long vs = vsize(c), np = pe - pb;
   const size_t budget = workspace_budget();
   int nc = (int)std::max<long long>(1, (long long)(budget * 0.8 / (2.0 * np * vs * sizeof(double2))));
-  nc = std::min(nc, nt);
+  nc = std::min(nc, nte);
   P.nc = nc;
   P.items_per_t = np;
-  std::vector<BdItem> A((size_t)nt * np), B((size_t)nt * np);
-  for (int t = 0; t < nt; ++t) {
+  std::vector<BdItem> A((size_t)nte * np), B((size_t)nte * np);
+  for (int t = 0; t < nte; ++t) {
     const int tl = t % nc;
     for (long long lp = 0; lp < np; ++lp) {
       const long long p = pb + lp;
@@ -805,7 +902,7 @@ static sgw_status build_p0_plan(sgw_ctx* c, ContractionPlan& P, long long pb, lo
   double work_t = 0;
   for (size_t b = 0; b < c->auxb_off.size(); ++b) work_t += (double)c->auxb_n[b] * c->auxb_n[b] * nao * nao * Nk;
   const long long target = unit_target(work_t * nc);
-  for (int t = 0; t < nt; ++t) {
+  for (int t = 0; t < nte; ++t) {
     if (t % nc == 0) {
       if (t > 0) schedule_units(units, (size_t)base, 0);
       base = (long long)units.size();
@@ -827,11 +924,13 @@ static sgw_status build_p0_plan(sgw_ctx* c, ContractionPlan& P, long long pb, lo
     }
   }
   schedule_units(units, (size_t)base, 0);
-  P.unit_start[nt] = units.size();
-  P.tile_start[nt] = tiles.size();
+  for (int t = nte; t <= nt; ++t) {
+    P.unit_start[t] = units.size();
+    P.tile_start[t] = tiles.size();
+  }
   P.max_units_chunk = 0;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
+  for (int t0 = 0; t0 < nte; t0 += nc) {
+    const int t1 = std::min(nte, t0 + nc);
     P.max_units_chunk = std::max(P.max_units_chunk, P.unit_start[t1] - P.unit_start[t0]);
   }
   P.fl_A_t = P.fl_B_t = P.fl_G_t = 0;
@@ -876,8 +975,8 @@ static sgw_status polarization_impl(sgw_ctx* c, const ContractionPlan& P, const 
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
   const std::string t_vg = std::string("p0_vg") + tag, t_gvg = std::string("p0_gvg") + tag,
                     t_gram = std::string("p0_gram") + tag;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
+  for (int t0 = 0; t0 < P.nt_eff; t0 += nc) {
+    const int t1 = std::min(P.nt_eff, t0 + nc);
     const long long ni = (long long)(t1 - t0) * np;
     const int ntc = t1 - t0;
     // Z[A][c][j] = sum_d V[A][c][d] G^{k+q}(tau)[d][j]
@@ -893,8 +992,7 @@ static sgw_status polarization_impl(sgw_ctx* c, const ContractionPlan& P, const 
     run(c, t_gram.c_str(), P.fl_G_t * ntc, 1, st, [&] { gram_partials(gg, X, V, P.d_units + u0, (int)(u1 - u0), part, st); });
     run(c, "gram_reduce", 0.0, 1, st, [&] { gram_reduce(P.d_tiles + ti0, (int)(ti1 - ti0), part, out, z(alpha), 0, st); });
   }
-  CKS(lower_from_upper(c, 1, out, st));
-  return SGW_OK;
+  return p0_complete(c, out, P.nt_eff, st);
 }
 
 static sgw_status polarization_range(sgw_ctx* c, const void* G_tau, void* P0_tau, long long pb, long long pe,

@@ -551,6 +551,46 @@ void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t 
   if (nitems > 0) k_hermitian_part<<<nitems, 256, 0, st>>>(items, X);
 }
 
+// P0 past the middle tau node from its partner block at the mirrored node: one CTA per (block,
+// tau), two plain n^3 steps through a scratch block, T = M S^T then M T^dagger read as T M^dagger:
+//   T[i][c] = sum_a M[i][a] S[c][a],   R[i][j] = sum_c T[i][c] conj(M[j][c]).
+__global__ void __launch_bounds__(256) k_p0_reflect(const ReflItem* __restrict__ items, double2* __restrict__ P0,
+                                                    long long p_elems, int nt, int h, const double2* __restrict__ M,
+                                                    double2* __restrict__ scratch) {
+  const ReflItem it = items[blockIdx.x];
+  const int t = h + blockIdx.y, n = it.n;
+  const double2* S = P0 + (long long)(nt - 1 - t) * p_elems + it.src_off;
+  const double2* Mb = M + it.m_off;
+  double2* T = scratch + (long long)blockIdx.y * p_elems + it.dst_off;
+  double2* R = P0 + (long long)t * p_elems + it.dst_off;
+  const int nn = n * n;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int i = e / n, cc = e - i * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int a = 0; a < n; ++a) {
+      const double2 m = Mb[(long long)i * n + a], x = S[(long long)cc * n + a];
+      acc.x = fma(m.x, x.x, fma(-m.y, x.y, acc.x));
+      acc.y = fma(m.x, x.y, fma(m.y, x.x, acc.y));
+    }
+    T[e] = acc;
+  }
+  __syncthreads();  // T is read across the CTA below (global writes of the block are visible after it)
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int cc = 0; cc < n; ++cc) {
+      const double2 x = T[(long long)i * n + cc], m = Mb[(long long)j * n + cc];  // x conj(m)
+      acc.x = fma(x.x, m.x, fma(x.y, m.y, acc.x));
+      acc.y = fma(x.y, m.x, fma(-x.x, m.y, acc.y));
+    }
+    R[e] = acc;
+  }
+}
+void p0_reflect(const ReflItem* items, int nitems, double2* P0, long long p_elems, int nt, int h, const double2* M,
+                double2* scratch, cudaStream_t st) {
+  if (nitems > 0 && nt > h) k_p0_reflect<<<dim3(nitems, nt - h), 256, 0, st>>>(items, P0, p_elems, nt, h, M, scratch);
+}
+
 // ---------------------------------------------------------------------------
 // Series map along the tau / frequency axis: out[m][e] = alpha sum_t T[m][t] in[t][e].
 // ---------------------------------------------------------------------------

@@ -102,6 +102,16 @@ void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_
 // Hermitian part of every block: X <- (X + X^dagger) / 2.
 void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t st);
 
+// tau reflection of P0 in block coordinates: for t in [h, nt) and every item (one auxiliary block
+// of a wedge point), P0[t][dst] = M_b P0[nt - 1 - t][src]^T M_b^dagger (M_b n x n at m_off);
+// scratch holds (nt - h) packed families.
+struct ReflItem {
+  long long dst_off, src_off, m_off;
+  int n, pad;
+};
+void p0_reflect(const ReflItem* items, int nitems, double2* P0, long long p_elems, int nt, int h, const double2* M,
+                double2* scratch, cudaStream_t st);
+
 // out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
 void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,
                 long long E, double2 alpha, int accumulate, cudaStream_t st);
@@ -174,6 +184,7 @@ struct TcPlan;  // tensor-core jobs of the chosen form (tc.cu)
 struct ContractionPlan {
   bool built = false;
   long long pb = 0, pe = 0;           // pair range [pb, pe) of the orientation's pair list it covers
+  int nt_eff = 0;                     // tau values contracted (the first ceil(nt/2) with the P0 reflection)
   int nc = 0;                         // tau values per chunk
   long long items_per_t = 0;          // block-multiply items per tau value
   BdItem *d_A = nullptr, *d_B = nullptr;
@@ -258,6 +269,12 @@ struct sgw_ctx {
   cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
   bool herm = false;  // frequency sets closed under w -> -w: Hermitian blocks are exploited
+  // P0^{q_w}(tau) for tau past the middle node from P0^{-q_w}(beta - tau) (set up by
+  // sgw_build_irrep_basis when every reflection matrix is block structured)
+  bool refl_ok = false;
+  sgw::ReflItem* d_refl = nullptr;
+  int n_refl = 0;
+  double2* d_reflM = nullptr;
   sgw::HermItem* d_herm_items[3] = {nullptr, nullptr, nullptr};  // Sigma~(tau), P0(tau), Sigma_HF blocks
   int n_herm_items[3] = {0, 0, 0};
   // iteration buffers and the captured graph
@@ -330,6 +347,12 @@ inline void run(sgw_ctx* c, const char* name, double flops, int nkern, cudaStrea
 
 sgw_status lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t st);
 size_t workspace_budget();  // bytes the contraction plans may size their intermediates for
+// tau values the P0 chains contract for the pair range [pb, pe) (all of them, or the first
+// ceil(nt/2) when the whole pair list is asked for and the reflection is set up)
+int p0_tau_count(const sgw_ctx* c, long long pb, long long pe);
+// P0 for the tau values past p0_tau_count by the reflection (after the chains, which wrote the
+// upper triangles of the first ones): mirror, reflect, mirror
+sgw_status p0_complete(sgw_ctx* c, double2* P0, int nt_eff, cudaStream_t st);
 double gram_elems(const sgw_ctx* c, int nb);  // elements a Gram stage contracts in a block of nb
 
 // tensor-core chains of the chosen form (tc.cu)

@@ -70,6 +70,7 @@ struct TcArgs {
 // Cached jobs of the tensor-core chains.
 struct TcPlan {
   long long pb = 0, pe = 0;            // pair range [pb, pe) of the orientation's pair list
+  int nt_eff = 0;                      // tau values the P0 chain contracts (the reflection gives the rest)
   bool built_p0 = false, built_sigma = false;
   long long unit_p0 = 0, unit_s = 0;   // split-K unit length of the Gram reductions (chunks)
   bool tuned_p0 = false, tuned_s = false;
@@ -930,13 +931,13 @@ long long nc_override() {
   return s ? std::max(1LL, std::atoll(s)) : 0;
 }
 
-long long tc_nc(const sgw_ctx* c, long long np) {
+long long tc_nc(const sgw_ctx* c, long long np, long long nt_eff) {
   const long long vs = (long long)c->naux * c->nao * c->nao;
   const double budget = (double)workspace_budget();
   long long nc = (long long)(budget * 0.6 / (2.0 * np * vs * sizeof(float2)));
-  nc = std::max(1LL, std::min<long long>({nc, (long long)c->nt, 128LL}));
-  const long long nchunks = (c->nt + nc - 1) / nc;
-  return (c->nt + nchunks - 1) / nchunks;  // balanced chunks
+  nc = std::max(1LL, std::min<long long>({nc, nt_eff, 128LL}));
+  const long long nchunks = (nt_eff + nc - 1) / nc;
+  return (nt_eff + nchunks - 1) / nchunks;  // balanced chunks
 }
 
 sgw_status tables_common(sgw_ctx* c, TcPlan& T) {
@@ -999,7 +1000,7 @@ void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long
 
 // Gram jobs of P0 for split-K units of `unit` chunks (replaces the previous tables).
 static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
-  const int Nk = c->Nk, nt = c->nt, nao = c->nao, nc = T.nc_p0;
+  const int Nk = c->Nk, nt = c->nt, nao = c->nao, nc = T.nc_p0, nte = T.nt_eff;
   const long long np = T.pe - T.pb;
   const int nch_g = (2 * nao * nao + 15) / 16;
   std::vector<TcJob> pg;
@@ -1008,8 +1009,8 @@ static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
   // Gram units per tau chunk over the tau-interleaved X: rows (Q, tl) of each pair slab
   std::vector<int2> prp;
   T.prp_start.assign(nt + 1, 0);
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
+  for (int t0 = 0; t0 < nte; t0 += nc) {
+    const int t1 = std::min(nte, t0 + nc);
     const long long slot0 = (long long)pg.size(), tile0 = (long long)pr.size();
     for (int t = t0; t < t1; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); T.prp_start[t] = prp.size(); }
     for (size_t b = 0; b < c->auxb_off.size(); ++b) {
@@ -1027,12 +1028,12 @@ static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
     }
     reduce_pieces(pr, tile0, (long long)pr.size(), prp);
   }
-  T.prp_start[nt] = prp.size();
+  for (int t = nte; t <= nt; ++t) T.prp_start[t] = prp.size();
   CKS(up(c, T.d_prp, prp));
-  T.pg_start[nt] = pg.size(); T.pr_start[nt] = pr.size();
+  for (int t = nte; t <= nt; ++t) { T.pg_start[t] = pg.size(); T.pr_start[t] = pr.size(); }
   T.max_units_p0 = 0;
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
+  for (int t0 = 0; t0 < nte; t0 += nc) {
+    const int t1 = std::min(nte, t0 + nc);
     T.max_units_p0 = std::max(T.max_units_p0, T.pg_start[t1] - T.pg_start[t0]);
   }
   (void)np;
@@ -1044,9 +1045,9 @@ static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
 static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   if (T.built_p0) return SGW_OK;
   CKS(tables_common(c, T));
-  const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
+  const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux, nte = T.nt_eff;
   const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
-  const int nc = T.nc_req_p0 > 0 ? (int)balanced_nc(nt, T.nc_req_p0) : (int)tc_nc(c, np);
+  const int nc = T.nc_req_p0 > 0 ? (int)balanced_nc(nte, T.nc_req_p0) : (int)tc_nc(c, np, nte);
   T.nc_p0 = nc;
   const int rows = naux * nao;
   T.mt_vg = (rows + 127) / 128;
@@ -1056,8 +1057,8 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   // V G jobs of a tau chunk in the order [pair][column tile][tau]: the nc units that read the same
   // V tile for the chunk's tau values run side by side, so V comes from memory once per chunk and
   // from L2 for the other tau values.  G(-tau) Z' jobs read a Z' tile per tau and keep tau order.
-  for (int t0 = 0; t0 < nt; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc);
+  for (int t0 = 0; t0 < nte; t0 += nc) {
+    const int t1 = std::min(nte, t0 + nc);
     const long long first = (long long)vg.size();
     for (int t = t0; t < t1; ++t) T.vg_start[t] = first;
     for (long long lp = 0; lp < np; ++lp)
@@ -1091,7 +1092,7 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
         }
     }
   }
-  T.vg_start[nt] = vg.size(); T.gvg_start[nt] = gvg.size();
+  for (int t = nte; t <= nt; ++t) { T.vg_start[t] = vg.size(); T.gvg_start[t] = gvg.size(); }
   T.unit_p0 = unit_override() ? unit_override() : kUnitDefault;
   if (unit_override()) T.tuned_p0 = true;  // a fixed unit holds for the context's lifetime
   CKS(build_p0_gram(c, T, T.unit_p0));
@@ -1164,7 +1165,7 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
   CKS(tables_common(c, T));
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux;
   const long long np = T.pe - T.pb;  // pairs of the range; intermediates are indexed by p - pb
-  const int nc = T.nc_req_s > 0 ? (int)balanced_nc(nt, T.nc_req_s) : (int)tc_nc(c, np);
+  const int nc = T.nc_req_s > 0 ? (int)balanced_nc(nt, T.nc_req_s) : (int)tc_nc(c, np, nt);
   T.nc_s = nc;
   T.slot_s = kSlotD;
   const long long vs = (long long)naux * nao * nao;
@@ -1269,6 +1270,7 @@ static TcPlan& plan_for(sgw_ctx* c, long long pb, long long pe) {
     t = new TcPlan();
     t->pb = pb;
     t->pe = pe;
+    t->nt_eff = p0_tau_count(c, pb, pe);
   }
   return *t;
 }
@@ -1353,14 +1355,15 @@ static sgw_status p0_run(sgw_ctx* c, TcPlan& T, const double2* G, double2* out, 
   CKS(make_map(c, &mXg, X, 2LL * nao * nao, (long long)naux * nc, np, 8LL * nao * nao, (long long)nc * vs * 8, 32));
   CKS(make_map(c, &mVg, c->d_V32[0], 2LL * nao * nao, naux, npg, 8LL * nao * nao, vs * 8, 64));
   const double alpha = c->p.loop_sign * (double)c->p.spin_factor / c->Nk;
-  const int t_end = trial_ms ? std::min(nt, nc) : nt, reps = trial_ms ? 2 : 1;
+  const int nte = T.nt_eff;  // tau values contracted (the reflection gives the rest)
+  const int t_end = trial_ms ? std::min(nte, nc) : nte, reps = trial_ms ? 2 : 1;
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (trial_ms && (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess))
     return c->fail(SGW_ERR_CUDA, "autotuner events");
   for (int rep = 0; rep < reps; ++rep) {
   if (trial_ms && rep == reps - 1) cudaEventRecord(ea, st);
   for (int t0 = 0; t0 < t_end; t0 += nc) {
-    const int t1 = std::min(nt, t0 + nc), ntc = t1 - t0;
+    const int t1 = std::min(nte, t0 + nc), ntc = t1 - t0;
     TcArgs a{};
     a.a_box = 128;
     a.b_rows = 64;
@@ -1415,7 +1418,7 @@ static sgw_status p0_run(sgw_ctx* c, TcPlan& T, const double2* G, double2* out, 
     return ok ? SGW_OK : c->fail(SGW_ERR_CUDA, "autotuner timing");
   }
   if (tune) T.tuned_p0 = true;
-  return lower_from_upper(c, 1, out, st);
+  return p0_complete(c, out, nte, st);
 }
 
 // Candidate tau chunks of the autotuner: the largest the workspace allows, about half and about a
@@ -1467,7 +1470,7 @@ sgw_status tc_polarization(sgw_ctx* c, const double2* G, double2* out, long long
       T.built_p0 = false;
       T.tuned_nc_p0 = true;
     } else if (autotune_enabled() && !capturing(st)) {
-      CKS(tune_nc(c, c->nt, tc_nc(c, T.pe - T.pb), T.nc_req_p0, T.built_p0, "P0", [&] { return build_p0(c, T); },
+      CKS(tune_nc(c, T.nt_eff, tc_nc(c, T.pe - T.pb, T.nt_eff), T.nc_req_p0, T.built_p0, "P0", [&] { return build_p0(c, T); },
                   [&](float* ms) { return p0_run(c, T, G, out, st, ms); }));
       T.tuned_nc_p0 = true;
     }
@@ -1595,7 +1598,7 @@ sgw_status tc_self_energy(sgw_ctx* c, const double2* G, const double2* P, double
       T.built_sigma = false;
       T.tuned_nc_s = true;
     } else if (autotune_enabled() && !capturing(st)) {
-      CKS(tune_nc(c, c->nt, tc_nc(c, T.pe - T.pb), T.nc_req_s, T.built_sigma, "Sigma",
+      CKS(tune_nc(c, c->nt, tc_nc(c, T.pe - T.pb, c->nt), T.nc_req_s, T.built_sigma, "Sigma",
                   [&] { return build_sigma(c, T); }, [&](float* ms) { return s_run(c, T, G, P, out, st, ms); }));
       T.tuned_nc_s = true;
     }
