@@ -261,7 +261,10 @@ SGW_API sgw_status sgw_self_energy_pairs(sgw_ctx* ctx, const void* G_tau, const 
  * Limits: 2 * nw_b * p_elems <= 4 Mi complex numbers and auxiliary blocks of at most 90;
  * larger problems get SGW_ERR_ARG with a message (use sgw_screened_interaction).  The
  * context must have run sgw_screened_interaction once (set-up that allocates the launch
- * tables this call reuses), else SGW_ERR_STATE.  The first call on a device looks up the
+ * tables this call reuses), else SGW_ERR_STATE; SGW_ERR_STATE too when the current device is
+ * not the one that was current at sgw_create.  A refused call writes nothing.  With
+ * sgw_profile_enable on, its kernels are counted as those of sgw_screened_interaction ("ft",
+ * "w_solve").  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current); make that first
  * call before any stream capture.  All calls share the array: calls that overlap on the GPU
  * (on different streams, or from different contexts) race and must be serialised by the

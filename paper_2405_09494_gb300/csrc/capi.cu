@@ -286,6 +286,7 @@ extern "C" SGW_API sgw_status sgw_create(const sgw_params* p, sgw_ctx** out) {
   c->nt = p->ntau;
   c->nwf = p->nw_f;
   c->nwb = p->nw_b;
+  if (cudaGetDevice(&c->device) != cudaSuccess) c->device = -1;
   sgw_status s = build_grid(c);
   if (s != SGW_OK) { delete c; return s; }
   auto upc = [&](double2*& d, const std::vector<cplx>& h) {

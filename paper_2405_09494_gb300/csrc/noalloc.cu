@@ -3,6 +3,7 @@
 // call in (for example code that runs while another component is capturing a CUDA graph,
 // where cudaMalloc is not permitted, or a host application that fixes its device memory
 // budget at start-up and forbids allocations afterwards).
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -28,6 +29,10 @@ sgw_status scratch_address(sgw_ctx* c, double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  // the context's tables and the scratch must be on one device: the array's address is per device
+  if (dev != c->device)
+    return c->fail(SGW_ERR_STATE, "sgw_screened_interaction_noalloc: the current device (" + std::to_string(dev) +
+                                      ") is not the context's (" + std::to_string(c->device) + ")");
   if (dev < 0 || dev >= kMaxDevices) return c->fail(SGW_ERR_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_mu);
   if (g_ptr[dev] == nullptr) {
@@ -71,10 +76,21 @@ extern "C" SGW_API sgw_status sgw_screened_interaction_noalloc(sgw_ctx* c, const
   double2* P0w = scr;                      // [nw_b][p_elems], fully overwritten below
   double2* Pw = scr + (size_t)c->nwb * pe;  // [nw_b][p_elems], fully overwritten below
   const double2 one = make_double2(1.0, 0.0);
-  series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, one, 0, st);
-  invert_plan(INV_W, c->w_plan, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, nullptr, c->d_status,
-              st);
-  series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, one, 0, st);
+  // the launch accounting of sgw_screened_interaction (it records CUDA events only, when profiling
+  // is on, and allocates no device memory)
+  const double flt = 8.0 * c->nwb * (double)c->nt * pe;
+  double flw = 0;
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) flw += 8.0 * c->nwb * std::pow((double)c->auxb_n[b], 3);
+  run(c, "ft", flt, 1, st, [&] {
+    series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, one, 0, st);
+  });
+  run(c, "w_solve", flw, 1, st, [&] {
+    invert_plan(INV_W, c->w_plan, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, nullptr,
+                c->d_status, st);
+  });
+  run(c, "ft", flt, 1, st, [&] {
+    series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, one, 0, st);
+  });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return c->fail(SGW_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return SGW_OK;

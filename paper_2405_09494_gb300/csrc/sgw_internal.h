@@ -201,6 +201,7 @@ struct sgw_ctx {
   sgw_params p{};
   std::vector<int> mats_f, mats_b;
   int Nk = 0, nao = 0, naux = 0, nt = 0, nwf = 0, nwb = 0;
+  int device = -1;  // CUDA device current at sgw_create; the context's memory lives there
   std::string last_error;
 
   // tau grid and transforms (host, row-major)
