@@ -44,14 +44,14 @@ if ROOT not in sys.path:
 
 METRIC = "scGW iteration time (s) and TFLOP/s vs tensor peak, mixed vs FP64 at stated error"
 DEFAULT_CONFIG = "c4"
-NOT_C5 = ("c5 (rocksalt, nao 104, naux 600, 200 tau) takes about a minute per chosen-form pass and tens of "
-          "minutes per plain pass, beyond a benchmark run; its loop is recorded separately")
+NOT_C5 = ("c5 (rocksalt, nao 104, naux 600, 200 tau) takes about 35 s per chosen-form pass and about half an "
+          "hour per plain pass, beyond a benchmark run; its loop is recorded separately")
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2070 MHz
 # DRAM bytes (read + write) per (pair, tau) unit of a kernel class, from one ncu capture of the same
 # kernel on the small case c3s (c3's tile sizes: nao 52, naux 300; profiles/k_tc_persist_c3s.md):
 # reported as the roofline's traffic, scaled by the units one launch processes, on workloads with
 # those tile sizes (c3, c4), while the kernel is unchanged.
-DRAM_BYTES_PER_UNIT = {"sigma_pvg_tc": (3.104321e9 + 2.457611e9) / (24 * 16)}
+DRAM_BYTES_PER_UNIT: dict = {}  # none yet for the current tensor-core kernel
 TRAFFIC_SIZES = {"c3", "c4", "c3s"}
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 

@@ -40,7 +40,7 @@ namespace sgw {
 struct alignas(16) TcJob {
   int a_y = 0, a_z = 0, b_y = 0, b_z = 0;  // first row and slab of the A and B boxes
   int a_x = 0, b_x = 0;    // first contracted coordinate (reals, multiple of 4)
-  int nslab = 1, nchunk = 1;  // contraction loop: nslab slabs x nchunk chunks of 16 reals
+  int nslab = 1, nchunk = 1;  // contraction loop: nslab slabs x nchunk chunks of 32 reals
   int a_dz = 0, b_dz = 0;  // slab increments
   int m_rows = 0;          // rows of A the job covers (tiles of 128)
   int n_valid = 0, n_mma = 16;  // stored columns; MMA width (multiple of 16, <= 128)
@@ -100,8 +100,13 @@ struct TcPlan {
 
 namespace {
 
-constexpr int kTileBytes = 128 * 64;         // 128 rows x 16 fp32 (one swizzle row each)
-constexpr int kStageBytes = 6 * kTileBytes;  // A head, A tail, B1 head, B1 tail, B2 head, B2 tail
+// One chunk of the contraction is 32 reals (a 128-byte swizzle row of FP32): an A tile of 128 rows
+// and the four 64-row B variants (B1 head, B2 head, B1 tail, B2 tail) per stage.
+constexpr int kChunkReals = 32;
+constexpr int kRowBytes = 4 * kChunkReals;           // 128
+constexpr int kABytes = 128 * kRowBytes;             // 16 KB
+constexpr int kBVarBytes = 64 * kRowBytes;           // 8 KB
+constexpr int kStageBytes = kABytes + 4 * kBVarBytes;  // 48 KB
 // Drain waits (copies in flight, MMAs issued) always allow 2 s: a CTA must not exit while a copy
 // into its shared memory can still land.  The pipeline waits use the context's limit (TcArgs).
 constexpr unsigned long long kDrainNs = 2000000000ULL;
@@ -164,10 +169,12 @@ __device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, 
 }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.  The
+// K steps of a chunk start 32, 64 and 96 bytes into the rows: the swizzle phase (address bits 7-9)
+// is that of the 1024-byte aligned tile, so the base offset field stays 0.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // Instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major, M = 128.
 __device__ __forceinline__ uint32_t tf32_idesc(int n) {
@@ -223,17 +230,18 @@ __device__ __forceinline__ float4 rot4(float4 a) { return make_float4(-a.y, a.x,
 // tensor-memory accumulator ring run on across units, so the loads of one tile overlap the
 // MMAs and the stores of the previous ones.
 //   warp 0        TMA producer (one lane): the boxes of one chunk per stage
-//   warp 1        tensor-memory owner; one lane issues 12 MMAs per chunk
-//   warps 4-7     splitter: TF32 head and tail of the staged operands (and the B variants of
-//                 the Gram form) in shared memory
+//   warp 1        tensor-memory owner; one lane issues 12 MMAs per chunk (4 K steps of 8 x 3)
+//   warps 4-7     splitter: TF32 head and tail of the staged A rows into tensor memory (and the
+//                 B variants of the Gram form in shared memory)
 //   warps 8-15    epilogue, two warpgroups, each one half of the accumulator columns (a warp
 //                 reads the 32 tensor-memory lanes of its rank within the warpgroup)
-// DRAIN: accumulator ring of 4 buffers of 128 columns (Re 64, Im 64); every kDrain chunks the
+// Tensor memory: 2 accumulator buffers of 128 columns (Re 64, Im 64) in [0, 256), the A head and
+// tail of the four stages (32 + 32 columns each) in [256, 512).  DRAIN: every kDrain chunks the
 // MMA warp moves to the next buffer and the epilogue adds the finished one into round-to-nearest
 // FP32 registers (the tensor core's own accumulation truncates), storing them at the end of the
-// unit.  Without DRAIN: 2 buffers of 256 columns (Re 128, Im 128), one per unit, read once.
+// unit.  Without DRAIN: one buffer per unit, read once.
 // All waits are bounded in time (status SGW_ERR_TIMEOUT, copies drained, tensor memory freed).
-constexpr int kDrain = 2;
+constexpr int kDrain = 1;
 constexpr int kPThreads = 512;
 constexpr int kPStages = 4;
 constexpr int kPSmem = kPStages * kStageBytes + 1024;
@@ -262,13 +270,12 @@ template <bool CONJ, bool DRAIN>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_persist(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                  const TcJob* __restrict__ jobs, const TcArgs args, long long nunits, int* __restrict__ status) {
-  // tensor memory: accumulator buffers (Re 64 + Im 64 columns each) in [0, 384), the A head and
-  // tail of the four stages (16 + 16 columns each) in [384, 512)
-  constexpr int NB = 3;                             // accumulator buffers
+  constexpr int NB = 2;                             // accumulator buffers
   constexpr uint32_t kBufCols = 128u;
   constexpr uint32_t kImOff = 64u;                  // Im accumulator column offset in a buffer
   constexpr int kHalf = 32;                         // columns per epilogue warpgroup
-  constexpr uint32_t kACol = 384u;                  // A stages in tensor memory
+  constexpr uint32_t kACol = 256u;                  // A stages in tensor memory (64 columns each)
+  static_assert(kACol + 64u * kPStages <= 512u && NB * kBufCols <= kACol, "tensor-memory plan");
   extern __shared__ unsigned char dsm_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_full[kPStages], bar_ready[kPStages], bar_empty[kPStages];
@@ -317,7 +324,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const TcJob& job = ui.job;
         const int abox = args.a_box;
         const int a_boxes = (ui.m_valid + abox - 1) / abox;
-        const uint32_t tx_bytes = (uint32_t)(a_boxes * abox * 64) + (uint32_t)(args.b_rows * 64 * (CONJ ? 1 : 4));
+        const uint32_t tx_bytes =
+            (uint32_t)(a_boxes * abox * kRowBytes) + (uint32_t)(args.b_rows * kRowBytes * (CONJ ? 1 : 4));
         // the job must describe copies that start on 16-byte boundaries and fit the stage; otherwise
         // nothing is issued, the status records it and the CTA stops
         if (abox <= 0 || 128 % abox != 0 || a_boxes * abox > 128 || args.b_rows != 64 || (job.a_x & 3) ||
@@ -335,16 +343,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
             break;
           }
           const int slab = kk / job.nchunk, ch = kk - slab * job.nchunk;
-          const int ax = job.a_x + 16 * ch, bx = job.b_x + 16 * ch;
+          const int ax = job.a_x + kChunkReals * ch, bx = job.b_x + kChunkReals * ch;
           const int az = job.a_z + slab * job.a_dz, bz = job.b_z + slab * job.b_dz;
           const uint32_t full = su32(&bar_full[s]);
           const uint32_t st = su32(sm + s * kStageBytes);
           mbar_expect_tx(full, tx_bytes);
-          for (int i = 0; i < a_boxes; ++i) tma_load3(st + i * abox * 64, &amap, ax, ui.a_y + abox * i, az, full);
+          for (int i = 0; i < a_boxes; ++i)
+            tma_load3(st + i * abox * kRowBytes, &amap, ax, ui.a_y + abox * i, az, full);
           if (CONJ)
-            tma_load3(st + 2 * kTileBytes, &bmap, bx, job.b_y, bz, full);
-          else  // the four variants in one box: [variant][b_rows rows][16 reals]
-            tma_load4(st + 2 * kTileBytes, &bmap, bx, job.b_y, 0, bz, full);
+            tma_load3(st + kABytes, &bmap, bx, job.b_y, bz, full);
+          else  // the four variants in one box: [variant][b_rows rows][32 reals]
+            tma_load4(st + kABytes, &bmap, bx, job.b_y, 0, bz, full);
         }
         if (!ok) break;
       }
@@ -389,11 +398,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
           tc_after();
           const uint32_t base = su32(sm + s * kStageBytes);
 #pragma unroll
-          for (int sub = 0; sub < 2; ++sub) {
-            const uint32_t o = 32u * sub;
-            const uint32_t ah = tmem + kACol + 32u * s + 8u * sub, al = ah + 16u;  // A head / tail in TMEM
-            const uint32_t bb = base + 2 * kTileBytes + o, vs = (uint32_t)args.b_rows * 64u;
-            const uint64_t bh = sw64_desc(bb), bl = sw64_desc(bb + 2 * vs);  // [head | i head], [tail | i tail]
+          for (int sub = 0; sub < kChunkReals / 8; ++sub) {
+            const uint32_t o = 32u * sub;  // bytes into the 128-byte rows
+            const uint32_t ah = tmem + kACol + 64u * s + 8u * sub, al = ah + 32u;  // A head / tail in TMEM
+            const uint32_t bb = base + kABytes + o, vs = (uint32_t)kBVarBytes;
+            const uint64_t bh = sw128_desc(bb), bl = sw128_desc(bb + 2 * vs);  // [head | i head], [tail | i tail]
             const uint32_t acc = (fresh && sub == 0) ? 0u : 1u;
             umma_tf32_ta(t_re, al, bh, idesc, acc);
             umma_tf32_ta(t_re, ah, bl, idesc, 1u);
@@ -433,29 +442,33 @@ __global__ void __launch_bounds__(kPThreads, 1)
           break;
         }
         unsigned char* st = sm + s * kStageBytes;
-        // A: this thread's row (tensor-memory lane) of the 64-byte-swizzled raw tile -> head and tail
-        // into the stage's tensor-memory columns (16-byte chunk c of row r sits at c ^ ((r >> 1) & 3))
+        // A: this thread's row (tensor-memory lane) of the 128-byte-swizzled raw tile -> head and tail
+        // into the stage's tensor-memory columns (16-byte chunk c of row r sits at c ^ (r & 7)), in
+        // two halves of 16 reals
         {
-          const float4* rowp = reinterpret_cast<const float4*>(st + row * 64);
-          float x[16], h[16], l[16];
+          const float4* rowp = reinterpret_cast<const float4*>(st + row * kRowBytes);
+          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + kACol + 64u * s;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float4 v = rowp[c ^ ((row >> 1) & 3)];
-            x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
-          }
+          for (int hf = 0; hf < 2; ++hf) {
+            float x[16], h[16], l[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            h[e] = tf32_rn(x[e]);
-            l[e] = tf32_rn(x[e] - h[e]);
+            for (int c = 0; c < 4; ++c) {
+              const float4 v = rowp[(4 * hf + c) ^ (row & 7)];
+              x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              h[e] = tf32_rn(x[e]);
+              l[e] = tf32_rn(x[e] - h[e]);
+            }
+            tmem_st16(ta + 16u * hf, h);
+            tmem_st16(ta + 32u + 16u * hf, l);
           }
-          const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + kACol + 32u * s;
-          tmem_st16(ta, h);
-          tmem_st16(ta + 16u, l);
           tmem_wait_st();
         }
         if (CONJ) {
-          const int vstride = args.b_rows * 4;  // float4s between variants
-          float4* b1h = reinterpret_cast<float4*>(st + 2 * kTileBytes);
+          constexpr int vstride = kBVarBytes / 16;  // float4s between variants
+          float4* b1h = reinterpret_cast<float4*>(st + kABytes);
           float4* b2h = b1h + vstride;
           float4* b1l = b1h + 2 * vstride;
           float4* b2l = b1h + 3 * vstride;
@@ -709,8 +722,8 @@ sgw_status get_encode(sgw_ctx* c) {
   return SGW_OK;
 }
 
-// 3-D map of FP32 data: dims (kreals, rows, slabs), boxes of 16 reals x box_rows rows, 64-byte swizzle,
-// zero fill outside the tensor.
+// 3-D map of FP32 data: dims (kreals, rows, slabs), boxes of one chunk (32 reals) x box_rows rows,
+// 128-byte swizzle, zero fill outside the tensor.
 sgw_status make_map(sgw_ctx* c, CUtensorMap* m, const void* base, long long kreals, long long rows, long long slabs,
                     long long row_bytes, long long slab_bytes, int box_rows = 32) {
   CKS(get_encode(c));
@@ -718,17 +731,17 @@ sgw_status make_map(sgw_ctx* c, CUtensorMap* m, const void* base, long long krea
     return c->fail(SGW_ERR_ARG, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[3] = {(cuuint64_t)kreals, (cuuint64_t)rows, (cuuint64_t)slabs};
   cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)slab_bytes};
-  cuuint32_t box[3] = {16, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)kChunkReals, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return c->fail(SGW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SGW_OK;
 }
 
 // 4-D map of the B operands that carry four variants: dims (kreals, rows, 4, slabs), one box of
-// 16 reals x box_rows rows x 4 variants per chunk.
+// 32 reals x box_rows rows x 4 variants per chunk.
 sgw_status make_map4(sgw_ctx* c, CUtensorMap* m, const void* base, long long kreals, long long rows, long long slabs,
                      long long row_bytes, long long var_bytes, long long slab_bytes, int box_rows) {
   CKS(get_encode(c));
@@ -737,10 +750,10 @@ sgw_status make_map4(sgw_ctx* c, CUtensorMap* m, const void* base, long long kre
     return c->fail(SGW_ERR_ARG, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[4] = {(cuuint64_t)kreals, (cuuint64_t)rows, 4, (cuuint64_t)slabs};
   cuuint64_t strides[3] = {(cuuint64_t)row_bytes, (cuuint64_t)var_bytes, (cuuint64_t)slab_bytes};
-  cuuint32_t box[4] = {16, (cuuint32_t)box_rows, 4, 1};
+  cuuint32_t box[4] = {(cuuint32_t)kChunkReals, (cuuint32_t)box_rows, 4, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return c->fail(SGW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SGW_OK;
@@ -792,10 +805,10 @@ void fr(T*& p) {
 int round16(int n) { return (n + 15) & ~15; }
 long long al256(long long bytes) { return (bytes + 255) & ~255LL; }
 
-// Split-K unit length of the Gram reductions (chunks of 16 reals): an environment value fixes it,
+// Split-K unit length of the Gram reductions (chunks of 32 reals): an environment value fixes it,
 // otherwise the autotuner picks one of kUnitCandidates on the first call of a context.
-constexpr long long kUnitDefault = 256;
-constexpr long long kUnitCandidates[] = {128, 256, 512};
+constexpr long long kUnitDefault = 128;
+constexpr long long kUnitCandidates[] = {64, 128, 256};
 long long unit_override() {
   const char* s = std::getenv("SGW_TC_KCHUNK");
   return s ? std::max(1LL, std::atoll(s)) : 0;
@@ -863,8 +876,8 @@ GramTiles gram_interleaved(std::vector<TcJob>& jobs, long long slot0, long long 
         j.b_y = proto.b_y + ntile * ni;
         j.a_z += r.slab0 * proto.a_dz;
         j.b_z += r.slab0 * proto.b_dz;
-        j.a_x += 16 * r.c0;
-        j.b_x += 16 * r.c0;
+        j.a_x += kChunkReals * r.c0;
+        j.b_x += kChunkReals * r.c0;
         j.nslab = r.nslab;
         j.nchunk = r.nch;
         j.n_valid = std::min(ntile, ncols - ntile * ni);
@@ -1002,7 +1015,7 @@ void tc_store_v(const sgw_ctx* c, int which, const double2* V, float2* out, long
 static sgw_status build_p0_gram(sgw_ctx* c, TcPlan& T, long long unit) {
   const int Nk = c->Nk, nt = c->nt, nao = c->nao, nc = T.nc_p0, nte = T.nt_eff;
   const long long np = T.pe - T.pb;
-  const int nch_g = (2 * nao * nao + 15) / 16;
+  const int nch_g = (2 * nao * nao + kChunkReals - 1) / kChunkReals;
   std::vector<TcJob> pg;
   std::vector<TcTile> pr;
   T.pg_start.assign(nt + 1, 0); T.pr_start.assign(nt + 1, 0);
@@ -1053,7 +1066,7 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
   T.mt_vg = (rows + 127) / 128;
   std::vector<TcJob> vg, gvg;
   T.vg_start.assign(nt + 1, 0); T.gvg_start.assign(nt + 1, 0);
-  const int nch_o = (2 * nao + 15) / 16;
+  const int nch_o = (2 * nao + kChunkReals - 1) / kChunkReals;
   // V G jobs of a tau chunk in the order [pair][column tile][tau]: the nc units that read the same
   // V tile for the chunk's tau values run side by side, so V comes from memory once per chunk and
   // from L2 for the other tau values.  G(-tau) Z' jobs read a Z' tile per tau and keep tau order.
@@ -1116,7 +1129,7 @@ static sgw_status build_p0(sgw_ctx* c, TcPlan& T) {
 // Gram jobs of Sigma~ for split-K units of `unit` chunks (replaces the previous tables).
 static sgw_status build_sigma_gram(sgw_ctx* c, TcPlan& T, long long unit) {
   const int Nk = c->Nk, nw = c->nwedge, nt = c->nt, nao = c->nao, naux = c->naux, nc = T.nc_s;
-  const int nch_g = (2 * naux * nao + 15) / 16;
+  const int nch_g = (2 * naux * nao + kChunkReals - 1) / kChunkReals;
   std::vector<TcJob> sg;
   std::vector<TcTile> sr;
   T.sg_start.assign(nt + 1, 0); T.sr_start.assign(nt + 1, 0);
@@ -1181,7 +1194,7 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
     info[3 * b] = s; info[3 * b + 1] = nb; info[3 * b + 2] = d;
     boff[b] = c->auxb_off[b];
     rmax = std::max(rmax, nb);
-    kmax = std::max(kmax, (d + 2 * nb + 15) / 16 * 16);
+    kmax = std::max(kmax, (d + 2 * nb + kChunkReals - 1) / kChunkReals * kChunkReals);
     wblocks[c->auxb_w[b]].push_back(b);
   }
   T.pt_rows = rmax;
@@ -1193,7 +1206,7 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
   T.mt_pvg = (rows_x + 127) / 128;
   std::vector<TcJob> svg, pvg;
   T.svg_start.assign(nt + 1, 0); T.pvg_start.assign(nt + 1, 0);
-  const int nch_o = (2 * nao + 15) / 16;
+  const int nch_o = (2 * nao + kChunkReals - 1) / kChunkReals;
   // Vt G jobs in the order [pair][column tile][tau] within a tau chunk (Vt read once per chunk, as
   // for P0); P^T X1 jobs read an X1 tile per tau and keep tau order
   for (int t0 = 0; t0 < nt; t0 += nc) {
@@ -1229,7 +1242,7 @@ static sgw_status build_sigma(sgw_ctx* c, TcPlan& T) {
             v.a_x = 2 * s - d;
             v.b_y = n0; v.b_z = tl * ninst + b;
             v.b_x = 0;
-            v.nslab = 1; v.nchunk = (d + 2 * nb + 15) / 16;
+            v.nslab = 1; v.nchunk = (d + 2 * nb + kChunkReals - 1) / kChunkReals;
             v.m_rows = rows_x; v.n_valid = std::min(64, nb - n0); v.n_mma = round16(v.n_valid);
             v.out_off = lp * nc * vs + (long long)tl * naux * nao + (long long)(s + n0) * nao;  // X2[p][i][tl][A'][b]
             pvg.push_back(v);

@@ -51,8 +51,8 @@ def _chain(sess):
     return G, mu, P0, P, Sig
 
 
-@pytest.mark.parametrize("form,unit,tol", [("plain", None, 1e-10), ("mixed", None, 1e-5), ("mixed", "128", 1e-5),
-                                           ("mixed", "256", 1e-5), ("mixed", "512", 1e-5)])
+@pytest.mark.parametrize("form,unit,tol", [("plain", None, 1e-10), ("mixed", None, 1e-5), ("mixed", "64", 1e-5),
+                                           ("mixed", "128", 1e-5), ("mixed", "256", 1e-5)])
 def test_c2_full_size_sampled(c2, form, unit, tol):
     from paper_2405_09494_gb300 import api, sgw
 
