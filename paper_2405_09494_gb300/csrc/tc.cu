@@ -229,7 +229,11 @@ __device__ __forceinline__ float4 rot4(float4 a) { return make_float4(-a.y, a.x,
 // u = blockIdx.x, blockIdx.x + gridDim.x, ...; the shared-memory stage ring and the
 // tensor-memory accumulator ring run on across units, so the loads of one tile overlap the
 // MMAs and the stores of the previous ones.
-//   warp 0        TMA producer (one lane): the boxes of one chunk per stage
+//   warps 0, 2, 3 TMA producers (one lane each): producer p issues the boxes of the chunks
+//                 g = p (mod 3) of the CTA's chunk sequence, each into stage g mod 4 once the
+//                 stage is free (an SM takes in about one box per 700-1000 clocks per issuing warp,
+//                 whatever the box size, so the copies of consecutive chunks come from different
+//                 warps)
 //   warp 1        tensor-memory owner; one lane issues 12 MMAs per chunk (4 K steps of 8 x 3)
 //   warps 4-7     splitter: TF32 head and tail of the staged A rows into tensor memory (and the
 //                 B variants of the Gram form in shared memory)
@@ -244,6 +248,10 @@ __device__ __forceinline__ float4 rot4(float4 a) { return make_float4(-a.y, a.x,
 constexpr int kDrain = 1;
 constexpr int kPThreads = 512;
 constexpr int kPStages = 4;
+constexpr int kNProd = 3;  // producer warps 0, 2, 3
+// A producer's consecutive chunks are kNProd apart, at most a ring's length: when it waits for
+// the release of a stage, the release before that one is already complete (no parity aliasing).
+static_assert(kNProd <= kPStages, "producer stride");
 constexpr int kPSmem = kPStages * kStageBytes + 1024;
 
 struct UnitInfo {
@@ -282,11 +290,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
   __shared__ __align__(8) uint64_t bar_accf[NB], bar_acce[NB], bar_done;
   __shared__ uint32_t tmem_holder;
   __shared__ volatile int abort_flag;
+  __shared__ unsigned long long last_chunk[kPStages];  // 1 + the last chunk issued on each stage (0: none)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < kPStages; ++s) {
+      last_chunk[s] = 0ULL;
       mbar_init(su32(&bar_full[s]), 1);
       mbar_init(su32(&bar_ready[s]), 128);
       mbar_init(su32(&bar_empty[s]), 1);
@@ -311,9 +321,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const uint32_t tmem = tmem_holder;
   const long long u_step = gridDim.x;
 
-  if (warp == 0) {
+  if (warp == 0 || warp == 2 || warp == 3) {
     if (lane == 0) {
-      // ---- producer
+      // ---- producers: every producer walks the whole chunk sequence and issues its own share
+      const int prod = warp == 0 ? 0 : warp - 1;
       long long gk = 0;  // chunk counter over all units of this CTA
       UnitInfo ui;
       TcJob nxt = load_job(jobs, args, blockIdx.x, nunits);
@@ -336,6 +347,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
         bool ok = true;
         for (int kk = 0; kk < ui.nk; ++kk, ++gk) {
+          if ((int)(gk % kNProd) != prod) continue;
           const int s = (int)(gk % kPStages);
           const long long round = gk / kPStages;
           if (round > 0 && !mbar_wait(su32(&bar_empty[s]), (uint32_t)((round - 1) & 1), &abort_flag, args.wait_ns)) {
@@ -354,13 +366,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
             tma_load3(st + kABytes, &bmap, bx, job.b_y, bz, full);
           else  // the four variants in one box: [variant][b_rows rows][32 reals]
             tma_load4(st + kABytes, &bmap, bx, job.b_y, 0, bz, full);
+          atomicMax(&last_chunk[s], (unsigned long long)(gk + 1));
         }
         if (!ok) break;
       }
-      // copies still in flight must land before the CTA exits: the last chunk issued on stage s
-      // is the largest g < gk with g = s (mod stages)
-      for (int s = 0; s < kPStages; ++s)
-        if (gk > s) mbar_wait(su32(&bar_full[s]), (uint32_t)(((gk - 1 - s) / kPStages) & 1), &abort_flag, kDrainNs, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -575,7 +584,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
     tc_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
-  if (threadIdx.x == 0 && abort_flag) atomicExch(status, (int)DEV_TIMEOUT);
+  if (threadIdx.x == 0) {
+    // copies still in flight must land before the CTA exits.  Only the last chunk issued on a stage
+    // can be: an earlier one was consumed before its stage could be issued again.
+    for (int s = 0; s < kPStages; ++s) {
+      const unsigned long long g1 = last_chunk[s];
+      if (g1 > 0) mbar_wait(su32(&bar_full[s]), (uint32_t)(((g1 - 1) / kPStages) & 1), &abort_flag, kDrainNs, false);
+    }
+    // a CTA that stopped records a timeout unless a malformed job was recorded first
+    if (abort_flag) atomicCAS(status, (int)DEV_OK, (int)DEV_TIMEOUT);
+  }
 }
 
 // out[tile] = alpha * sum over the tile's units of their FP32 partial tiles ([n][128] slots),
