@@ -51,7 +51,7 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 
 # kernel on the small case c3s (c3's tile sizes: nao 52, naux 300; profiles/k_tc_persist_c3s.md):
 # reported as the roofline's traffic, scaled by the units one launch processes, on workloads with
 # those tile sizes (c3, c4), while the kernel is unchanged.
-DRAM_BYTES_PER_UNIT: dict = {}  # none yet for the current tensor-core kernel
+DRAM_BYTES_PER_UNIT = {"sigma_pvg_tc": (3.156093e9 + 2.457867e9) / (24 * 16)}
 TRAFFIC_SIZES = {"c3", "c4", "c3s"}
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 
