@@ -318,7 +318,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   cudaDeviceSynchronize();
   dfree(c->d_TF); dfree(c->d_TFbar); dfree(c->d_TB); dfree(c->d_TBbar);
   dfree(c->d_beta_row); dfree(c->d_gl_interp); dfree(c->d_nu_f); dfree(c->d_tau);
-  dfree(c->d_Uao); dfree(c->d_Uaux); dfree(c->d_refl); dfree(c->d_reflM);
+  dfree(c->d_Uao); dfree(c->d_Uaux); dfree(c->d_refl); dfree(c->d_reflM); dfree(c->d_refl_tiles);
   dfree(c->d_ao_start); dfree(c->d_ao_size); dfree(c->d_ao_doff);
   dfree(c->d_aux_start); dfree(c->d_aux_size); dfree(c->d_aux_doff);
   dfree(c->d_full_start); dfree(c->d_full_size); dfree(c->d_full_doff);
@@ -330,7 +330,7 @@ extern "C" SGW_API sgw_status sgw_destroy(sgw_ctx* c) {
   free_plan(c->plan_p0); free_plan(c->plan_sigma); free_plan(c->plan_k); free_plan(c->plan_rho);
   free_plan(c->plan_p0_part); free_plan(c->plan_sigma_part);
   dfree(c->d_ws); dfree(c->d_g32); dfree(c->d_status); dfree(c->d_scalar); dfree(c->d_maxbits);
-  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab);
+  dfree(c->d_w_items); dfree(c->d_dy_items); dfree(c->d_hf_tab); dfree(c->d_wh_items); dfree(c->d_wh_adj);
   for (auto& h : c->d_herm_items) dfree(h);
   for (auto& a : c->inv_aux)
     if (a) cudaStreamDestroy(a);
@@ -380,8 +380,10 @@ extern "C" SGW_API sgw_status sgw_sync(sgw_ctx* c, sgw_stream stream) {
 static sgw_status setup_p0_reflection(sgw_ctx* c) {
   c->refl_ok = false;
   c->n_refl = 0;
+  c->n_refl_tiles = 0;
   dfree(c->d_refl);
   dfree(c->d_reflM);
+  dfree(c->d_refl_tiles);
   const char* e = std::getenv("SGW_P0_REFLECT");
   if ((e && e[0] == '0') || c->nt < 2) return SGW_OK;
   const int n = c->naux, n1 = c->p.nk[0], n2 = c->p.nk[1], n3 = c->p.nk[2];
@@ -438,9 +440,17 @@ static sgw_status setup_p0_reflection(sgw_ctx* c) {
       doff += (long long)nb * nb;
     }
   }
+  std::vector<ReflTile> tiles;
+  for (size_t i = 0; i < items.size(); ++i) {
+    const int nt32 = (items[i].n + 31) / 32;
+    for (int ti = 0; ti < nt32; ++ti)
+      for (int tj = 0; tj < nt32; ++tj) tiles.push_back({(int)i, ti, tj, 0});
+  }
   CKS(upload(c, c->d_refl, items));
   CKS(upload(c, c->d_reflM, Ms));
+  CKS(upload(c, c->d_refl_tiles, tiles));
   c->n_refl = (int)items.size();
+  c->n_refl_tiles = (int)tiles.size();
   c->refl_ok = true;
   return SGW_OK;
 }
@@ -455,8 +465,8 @@ sgw_status sgw::p0_complete(sgw_ctx* c, double2* P0, int nt_eff, cudaStream_t st
   if (nt_eff >= c->nt) return SGW_OK;
   const size_t need = (size_t)(c->nt - nt_eff) * c->p_elems;
   CKS(ensure_workspace(c, need * sizeof(double2)));
-  run(c, "p0_reflect", 0.0, 1, st, [&] {
-    p0_reflect(c->d_refl, c->n_refl, P0, c->p_elems, c->nt, nt_eff, c->d_reflM, c->d_ws, st);
+  run(c, "p0_reflect", 0.0, 2, st, [&] {
+    p0_reflect(c->d_refl, c->d_refl_tiles, c->n_refl_tiles, P0, c->p_elems, c->nt, nt_eff, c->d_reflM, c->d_ws, st);
   });
   return lower_from_upper(c, 1, P0, st);  // exactly Hermitian blocks (the products are, up to rounding)
 }
@@ -1053,6 +1063,34 @@ static sgw_status ensure_tables(sgw_ctx* c) {
       it.weight = z(0.0);
       w.push_back(it);
     }
+  // With a bosonic set closed under n -> -n and sorted, the W blocks at -Omega_n are the adjoints of
+  // those at Omega_n (P0(tau) blocks are Hermitian, so P0(-i Omega) = P0(i Omega)^dagger, and W
+  // inherits it): only rows [wh_m0, nw_b) are solved, each row m < wh_m0 is the adjoint of row
+  // nw_b - 1 - m.
+  std::vector<InvItem> wh;
+  std::vector<AdjItem> adj;
+  c->wh_m0 = -1;
+  {
+    bool sym = c->herm;
+    for (int m = 0; m < c->nwb && sym; ++m)
+      sym = c->mats_b[c->nwb - 1 - m] == -c->mats_b[m] && (m == 0 || c->mats_b[m] > c->mats_b[m - 1]);
+    if (sym) {
+      int m0 = 0;
+      while (m0 < c->nwb && c->mats_b[m0] < 0) ++m0;
+      c->wh_m0 = m0;
+      for (const InvItem& it : w)
+        if (it.m >= m0) wh.push_back(it);
+      for (int m = 0; m < m0; ++m)
+        for (size_t b = 0; b < c->auxb_off.size(); ++b) {
+          AdjItem a;
+          a.src_off = (long long)(c->nwb - 1 - m) * c->p_elems + c->auxb_off[b];
+          a.dst_off = (long long)m * c->p_elems + c->auxb_off[b];
+          a.n = c->auxb_n[b];
+          a.pad = 0;
+          adj.push_back(a);
+        }
+    }
+  }
   std::vector<InvItem> d;
   for (int m = 0; m < c->nwf; ++m)
     for (size_t b = 0; b < c->aob_off.size(); ++b) {
@@ -1102,6 +1140,12 @@ static sgw_status ensure_tables(sgw_ctx* c) {
   };
   split(w, c->w_plan);
   split(d, c->dy_plan);
+  if (c->wh_m0 >= 0) {
+    split(wh, c->wh_plan);
+    CKS(upload(c, c->d_wh_items, wh));
+    CKS(upload(c, c->d_wh_adj, adj));
+    c->n_wh_adj = (int)adj.size();
+  }
   if (c->w_plan.max_n > 1024 || c->dy_plan.max_n > 1024)
     return c->fail(SGW_ERR_ARG, "irrep blocks above 1024 are not supported by the inversion kernels");
   CKS(upload(c, c->d_w_items, w));
@@ -1113,7 +1157,7 @@ static sgw_status ensure_tables(sgw_ctx* c) {
     for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&c->inv_aux[i], cudaStreamNonBlocking));
     for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&c->inv_ev[i], cudaEventDisableTiming));
   }
-  for (InvPlan* pl : {&c->w_plan, &c->dy_plan}) {
+  for (InvPlan* pl : {&c->w_plan, &c->dy_plan, &c->wh_plan}) {
     pl->aux[0] = c->inv_aux[0];
     pl->aux[1] = c->inv_aux[1];
     pl->fork = c->inv_ev[0];
@@ -1122,6 +1166,7 @@ static sgw_status ensure_tables(sgw_ctx* c) {
   }
   c->w_plan.items = c->d_w_items;
   c->dy_plan.items = c->d_dy_items;
+  c->wh_plan.items = c->d_wh_items;
   c->tables = true;
   return SGW_OK;
 }
@@ -1143,15 +1188,20 @@ extern "C" SGW_API sgw_status sgw_screened_interaction(sgw_ctx* c, const void* P
   double2* Pw = P0w + (size_t)c->nwb * pe;
   double2* scr = Pw + (size_t)c->nwb * pe;
   const double flt = 8.0 * c->nwb * (double)c->nt * pe;
+  // rows [m0, nw_b) are transformed and solved; with the adjoint relation the rest are filled
+  const int m0 = c->wh_m0 >= 0 ? c->wh_m0 : 0, nsolve = c->nwb - m0;
+  const InvPlan& wp = c->wh_m0 >= 0 ? c->wh_plan : c->w_plan;
   double flw = 0;
-  for (size_t b = 0; b < c->auxb_n.size(); ++b) flw += 8.0 * c->nwb * std::pow((double)c->auxb_n[b], 3);
-  run(c, "ft", flt, 1, st, [&] {
-    series_map(c->d_TB, c->nwb, c->nt, static_cast<const double2*>(P0_tau), pe, P0w, pe, pe, z(1.0), 0, st);
+  for (size_t b = 0; b < c->auxb_n.size(); ++b) flw += 8.0 * nsolve * std::pow((double)c->auxb_n[b], 3);
+  run(c, "ft", 8.0 * nsolve * (double)c->nt * pe, 1, st, [&] {
+    series_map(c->d_TB + (size_t)m0 * c->nt, nsolve, c->nt, static_cast<const double2*>(P0_tau), pe,
+               P0w + (size_t)m0 * pe, pe, pe, z(1.0), 0, st);
   });
   run(c, "w_solve", flw, 1, st, [&] {
-    invert_plan(INV_W, c->w_plan, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, scr, c->d_status,
-                st);
+    invert_plan(INV_W, wp, P0w, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr, Pw, nullptr, scr, c->d_status, st);
   });
+  if (c->wh_m0 > 0)
+    run(c, "w_mirror", 0.0, 1, st, [&] { block_adjoint(c->d_wh_adj, c->n_wh_adj, Pw, st); });
   run(c, "ft", flt, 1, st, [&] {
     series_map(c->d_TBbar, c->nt, c->nwb, Pw, pe, static_cast<double2*>(P_tau), pe, pe, z(1.0), 0, st);
   });

@@ -551,44 +551,97 @@ void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t 
   if (nitems > 0) k_hermitian_part<<<nitems, 256, 0, st>>>(items, X);
 }
 
-// P0 past the middle tau node from its partner block at the mirrored node: one CTA per (block,
-// tau), two plain n^3 steps through a scratch block, T = M S^T then M T^dagger read as T M^dagger:
-//   T[i][c] = sum_a M[i][a] S[c][a],   R[i][j] = sum_c T[i][c] conj(M[j][c]).
-__global__ void __launch_bounds__(256) k_p0_reflect(const ReflItem* __restrict__ items, double2* __restrict__ P0,
+// P0 past the middle tau node from its partner block at the mirrored node, in two launches over
+// 32 x 32 output tiles of every block (one CTA per tile and tau value, so a large block spreads
+// over many SMs):
+//   step 0: T[i][c] = sum_a M[i][a] S[c][a]            (T in scratch, S = P0 at beta - tau)
+//   step 1: R[i][j] = sum_c T[i][c] conj(M[j][c])     (R = P0 at tau)
+// Both are C[i][j] = sum_k A[i][k] op(B[j][k]); k runs in steps of 16 through shared memory
+// (A and B tiles stored k-major, padded rows); a thread holds 4 outputs of one column.
+template <int STEP>
+__global__ void __launch_bounds__(256) k_p0_reflect(const ReflItem* __restrict__ items,
+                                                    const ReflTile* __restrict__ tiles, double2* __restrict__ P0,
                                                     long long p_elems, int nt, int h, const double2* __restrict__ M,
                                                     double2* __restrict__ scratch) {
-  const ReflItem it = items[blockIdx.x];
+  __shared__ double2 As[16][33], Bs[16][33];
+  const ReflTile tl = tiles[blockIdx.x];
+  const ReflItem it = items[tl.item];
   const int t = h + blockIdx.y, n = it.n;
-  const double2* S = P0 + (long long)(nt - 1 - t) * p_elems + it.src_off;
-  const double2* Mb = M + it.m_off;
-  double2* T = scratch + (long long)blockIdx.y * p_elems + it.dst_off;
-  double2* R = P0 + (long long)t * p_elems + it.dst_off;
-  const int nn = n * n;
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = e / n, cc = e - i * n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int a = 0; a < n; ++a) {
-      const double2 m = Mb[(long long)i * n + a], x = S[(long long)cc * n + a];
-      acc.x = fma(m.x, x.x, fma(-m.y, x.y, acc.x));
-      acc.y = fma(m.x, x.y, fma(m.y, x.x, acc.y));
-    }
-    T[e] = acc;
+  const double2* A;
+  const double2* B;
+  double2* C;
+  if (STEP == 0) {
+    A = M + it.m_off;
+    B = P0 + (long long)(nt - 1 - t) * p_elems + it.src_off;
+    C = scratch + (long long)blockIdx.y * p_elems + it.dst_off;
+  } else {
+    A = scratch + (long long)blockIdx.y * p_elems + it.dst_off;
+    B = M + it.m_off;
+    C = P0 + (long long)t * p_elems + it.dst_off;
   }
-  __syncthreads();  // T is read across the CTA below (global writes of the block are visible after it)
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int cc = 0; cc < n; ++cc) {
-      const double2 x = T[(long long)i * n + cc], m = Mb[(long long)j * n + cc];  // x conj(m)
-      acc.x = fma(x.x, m.x, fma(x.y, m.y, acc.x));
-      acc.y = fma(x.y, m.x, fma(-x.x, m.y, acc.y));
+  const int i0 = 32 * tl.ti, j0 = 32 * tl.tj;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double2 zero = make_double2(0.0, 0.0);
+  double2 acc[4] = {zero, zero, zero, zero};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    for (int e = threadIdx.x; e < 512; e += 256) {
+      const int r = e >> 4, kk = e & 15, k = k0 + kk;
+      const int ia = i0 + r, jb = j0 + r;
+      As[kk][r] = (ia < n && k < n) ? A[(long long)ia * n + k] : zero;
+      Bs[kk][r] = (jb < n && k < n) ? B[(long long)jb * n + k] : zero;
     }
-    R[e] = acc;
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; ++kk) {
+      double2 b = Bs[kk][tx];
+      if (STEP == 1) b.y = -b.y;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r] = cfma(As[kk][ty + 8 * r], b, acc[r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 8 * r, j = j0 + tx;
+    if (i < n && j < n) C[(long long)i * n + j] = acc[r];
   }
 }
-void p0_reflect(const ReflItem* items, int nitems, double2* P0, long long p_elems, int nt, int h, const double2* M,
-                double2* scratch, cudaStream_t st) {
-  if (nitems > 0 && nt > h) k_p0_reflect<<<dim3(nitems, nt - h), 256, 0, st>>>(items, P0, p_elems, nt, h, M, scratch);
+void p0_reflect(const ReflItem* items, const ReflTile* tiles, int ntiles, double2* P0, long long p_elems, int nt, int h,
+                const double2* M, double2* scratch, cudaStream_t st) {
+  if (ntiles <= 0 || nt <= h) return;
+  const dim3 grid(ntiles, nt - h);
+  k_p0_reflect<0><<<grid, 256, 0, st>>>(items, tiles, P0, p_elems, nt, h, M, scratch);
+  k_p0_reflect<1><<<grid, 256, 0, st>>>(items, tiles, P0, p_elems, nt, h, M, scratch);
+}
+
+// dst = src^dagger per item: one CTA per item walks 32 x 32 tiles through shared memory (rows read
+// and written along the fast index; the padded tile keeps each 8-lane phase on distinct banks).
+__global__ void __launch_bounds__(256) k_block_adjoint(const AdjItem* __restrict__ items, double2* __restrict__ X) {
+  __shared__ double2 tile[32][33];
+  const AdjItem it = items[blockIdx.x];
+  const int n = it.n;
+  const double2* S = X + it.src_off;
+  double2* D = X + it.dst_off;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < n; i0 += 32)
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        if (i < n && j < n) tile[r][tx] = S[(long long)i * n + j];
+      }
+      __syncthreads();
+      for (int r = ty; r < 32; r += 8) {  // D[j0 + r][i0 + tx] = conj(S[i0 + tx][j0 + r])
+        const int dr = j0 + r, dc = i0 + tx;
+        if (dr < n && dc < n) {
+          const double2 v = tile[tx][r];
+          D[(long long)dr * n + dc] = make_double2(v.x, -v.y);
+        }
+      }
+      __syncthreads();
+    }
+}
+void block_adjoint(const AdjItem* items, int nitems, double2* X, cudaStream_t st) {
+  if (nitems > 0) k_block_adjoint<<<nitems, 256, 0, st>>>(items, X);
 }
 
 // ---------------------------------------------------------------------------

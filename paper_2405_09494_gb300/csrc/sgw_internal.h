@@ -102,6 +102,14 @@ void hermitian_fill(const HermItem* items, int nitems, double2* out, cudaStream_
 // Hermitian part of every block: X <- (X + X^dagger) / 2.
 void hermitian_part(const HermItem* items, int nitems, double2* X, cudaStream_t st);
 
+// dst = src^dagger per block (conjugate transpose between two blocks of the same size): W at a
+// negative bosonic frequency from W at the mirrored positive one.
+struct AdjItem {
+  long long src_off, dst_off;
+  int n, pad;
+};
+void block_adjoint(const AdjItem* items, int nitems, double2* X, cudaStream_t st);
+
 // tau reflection of P0 in block coordinates: for t in [h, nt) and every item (one auxiliary block
 // of a wedge point), P0[t][dst] = M_b P0[nt - 1 - t][src]^T M_b^dagger (M_b n x n at m_off);
 // scratch holds (nt - h) packed families.
@@ -109,8 +117,12 @@ struct ReflItem {
   long long dst_off, src_off, m_off;
   int n, pad;
 };
-void p0_reflect(const ReflItem* items, int nitems, double2* P0, long long p_elems, int nt, int h, const double2* M,
-                double2* scratch, cudaStream_t st);
+// the 32 x 32 output tiles of every item (tile row ti, column tj)
+struct ReflTile {
+  int item, ti, tj, pad;
+};
+void p0_reflect(const ReflItem* items, const ReflTile* tiles, int ntiles, double2* P0, long long p_elems, int nt, int h,
+                const double2* M, double2* scratch, cudaStream_t st);
 
 // out[m][e] = alpha * sum_t T[m][t] in[t * in_ld + e] (+ out if accumulate); T complex (nm x nt).
 void series_map(const double2* T, int nm, int nt, const double2* in, long long in_ld, double2* out, long long out_ld,
@@ -266,6 +278,13 @@ struct sgw_ctx {
   sgw::InvItem *d_w_items = nullptr, *d_dy_items = nullptr;
   int n_w_items = 0, n_dy_items = 0;
   sgw::InvPlan w_plan, dy_plan;   // W solve and Dyson batches (items above, side streams below)
+  // W solve over the non-negative bosonic frequencies only (frequency sets closed under
+  // n -> -n, sorted): rows [wh_m0, nw_b) are solved, the rest filled as adjoints; wh_m0 < 0: off
+  int wh_m0 = -1;
+  sgw::InvItem* d_wh_items = nullptr;
+  sgw::InvPlan wh_plan;
+  sgw::AdjItem* d_wh_adj = nullptr;
+  int n_wh_adj = 0;
   cudaStream_t inv_aux[2] = {nullptr, nullptr};
   cudaEvent_t inv_ev[3] = {nullptr, nullptr, nullptr};
   long long* d_hf_tab = nullptr;  // gamma scatter table (dense offsets, packed offsets, sizes, V offsets)
@@ -275,6 +294,8 @@ struct sgw_ctx {
   bool refl_ok = false;
   sgw::ReflItem* d_refl = nullptr;
   int n_refl = 0;
+  sgw::ReflTile* d_refl_tiles = nullptr;
+  int n_refl_tiles = 0;
   double2* d_reflM = nullptr;
   sgw::HermItem* d_herm_items[3] = {nullptr, nullptr, nullptr};  // Sigma~(tau), P0(tau), Sigma_HF blocks
   int n_herm_items[3] = {0, 0, 0};
