@@ -179,18 +179,20 @@ def test_diamond_nonsymmorphic_chain(diamond):
 
 
 def test_rocksalt_uses_hermitian_blocks(rocksalt):
-    """Frequency sets closed under w -> -w: the Gram stages fill the lower triangles by transposition."""
+    """Frequency sets closed under w -> -w: the Gram stages fill the lower triangles by transposition,
+    and the W solve covers the non-negative bosonic frequencies (the rest are adjoints)."""
     from paper_2405_09494_gb300 import sgw
 
     kernels = set(sgw.sgw_profile_read(rocksalt.sess.ctx))
-    assert {"p0_mirror", "sigma_mirror"} <= kernels, kernels
+    assert {"p0_mirror", "sigma_mirror", "w_mirror"} <= kernels, kernels
     P0u = rocksalt.unf(1, rocksalt.lP0)
     assert np.abs(P0u - P0u.conj().transpose(0, 1, 3, 2)).max() < 1e-12 * np.abs(P0u).max()
 
 
 def test_asymmetric_frequency_sets_contract_every_tile():
     """A bosonic and a fermionic set that are not closed under w -> -w: P(tau) and Sigma~(tau) lose
-    exact Hermiticity, so the library contracts every Gram tile; the chain still matches the oracle."""
+    exact Hermiticity, so the library contracts every Gram tile and solves W at every frequency; the
+    chain still matches the oracle."""
     _need_gpu()
     from paper_2405_09494_gb300 import sgw
 
@@ -202,7 +204,7 @@ def test_asymmetric_frequency_sets_contract_every_tile():
     case = Case(dataclasses.replace(cfg, name="rocksalt-asym", mats_b=mb, mats_f=mf))
     try:
         kernels = set(sgw.sgw_profile_read(case.sess.ctx))
-        assert not ({"p0_mirror", "sigma_mirror"} & kernels), kernels
+        assert not ({"p0_mirror", "sigma_mirror", "w_mirror"} & kernels), kernels
         assert rel_err(case.unf(1, case.lP0), case.P0) < TOL
         assert rel_err(case.unf(1, case.lP), case.P) < TOL
         assert rel_err(case.unf(0, case.lSig), case.Sig) < TOL
