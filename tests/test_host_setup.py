@@ -7,6 +7,8 @@
 * Block sizes at Gamma follow the textbook decomposition of the orbital
   representation (e.g. O_h: s -> A1g, p -> T1u, d -> Eg + T2g) and every
   partition covers the basis.
+* Every workload's Matsubara sets are sorted and mirror-symmetric (the Hermitian shortcuts and the
+  half-frequency W solve depend on it).
 """
 import json
 import os
@@ -138,3 +140,21 @@ def test_largest_workload_grid_is_closed_and_well_conditioned():
     rows = [0, 57, 100, 199]
     oTF = grid.forward_map([cfg.mats_f[i] for i in rows], cfg.beta, cfg.ntau, "F")
     assert np.abs(oTF - TF[rows]).max() < 1e-12 * np.abs(TF).max()
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4", "c5", "c3s", "t1"])
+def test_every_workload_frequency_set_is_sorted_and_mirror_symmetric(name):
+    """Each workload's Matsubara sets hold at least n_tau indices, ascend strictly, and are closed under
+    w -> -w with mirrored positions: fermionic index m and -m - 1 at positions i and n_w - 1 - i,
+    bosonic m and -m likewise (0 in the middle).  The Hermitian Gram stages need the closure.  The
+    W solve over the non-negative bosonic frequencies, whose other half are adjoints, needs the
+    bosonic order."""
+    from paper_2405_09494_gb300 import configs
+
+    cfg = configs.get(name)
+    mf, mb = list(cfg.mats_f), list(cfg.mats_b)
+    assert len(mf) >= cfg.ntau and len(mb) >= cfg.ntau
+    assert all(a < b for a, b in zip(mf, mf[1:])) and all(a < b for a, b in zip(mb, mb[1:]))
+    assert all(mf[len(mf) - 1 - i] == -mf[i] - 1 for i in range(len(mf)))
+    assert all(mb[len(mb) - 1 - i] == -mb[i] for i in range(len(mb)))
+    assert 0 in mb
