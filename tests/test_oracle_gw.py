@@ -8,7 +8,8 @@ What fixes each oracle function (none of these re-types the function itself):
   from the eigenvectors; Hermiticity; P0^{-q}(tau) = P0^q(beta - tau)^T;
   P0(i Omega_0) <= 0 with the physical loop sign.
 * screened_interaction (Eq. (P02P)): the Neumann series at weak coupling;
-  [P, P0] = 0 per frequency; Hermiticity in tau.
+  [P, P0] = 0 per frequency; Hermiticity in tau; the values at -Omega_n are the adjoints of those
+  at Omega_n on a closed frequency set.
 * self_energy (Eq. (sigma)): the trace identity
   sum_k Tr[Sigma^(2)k(tau) G^k(-tau)] = -(1/s) sum_q sum_QQ' P0^q_QQ'(tau) P0^{-q}_QQ'(tau)
   that ties its index structure to the pinned P0; Hermiticity; real inputs at
@@ -345,6 +346,31 @@ def test_screened_interaction_neumann_series(small):
     np.testing.assert_allclose(Pw, ref, atol=1e-15, rtol=1e-12)
     np.testing.assert_allclose(Pw @ P0w, P0w @ Pw, atol=1e-15)
     np.testing.assert_allclose(P, P.conj().transpose(0, 1, 3, 2), atol=1e-12)
+
+
+def test_screened_interaction_at_mirrored_frequencies_is_the_adjoint(small):
+    """With Hermitian P0(tau) blocks and a bosonic set closed under Omega -> -Omega, P0 and the
+    solve [I - P0]^{-1} P0 at -Omega_n are the adjoints of their values at Omega_n: a solver may
+    handle the non-negative frequencies and fill the rest.  An anti-Hermitian part in P0(tau)
+    breaks it."""
+    ops = small["ops"]
+    P0 = gw.polarization(small["G"], small["V"], NK)
+    mb = list(ops["mats_b"])
+    mirror = [mb.index(-n) for n in mb]
+
+    def residuals(P0_tau):
+        _, P0w, Pw = gw.screened_interaction(P0_tau, ops["TB"], ops["TBbar"])
+        r0 = np.abs(P0w[:, mirror] - P0w.conj().transpose(0, 1, 3, 2)).max() / np.abs(P0w).max()
+        r1 = np.abs(Pw[:, mirror] - Pw.conj().transpose(0, 1, 3, 2)).max() / np.abs(Pw).max()
+        return r0, r1
+
+    r0, r1 = residuals(P0)
+    assert r0 < 1e-13 and r1 < 1e-12, (r0, r1)
+    rng = np.random.default_rng(3)
+    H = rng.standard_normal(P0.shape) + 1j * rng.standard_normal(P0.shape)
+    H = 0.5 * (H + H.conj().transpose(0, 1, 3, 2))
+    s0, s1 = residuals(P0 + 1e-3 * np.abs(P0).max() * 1j * H)  # i H is anti-Hermitian
+    assert s0 > 1e-5 and s1 > 1e-5, (s0, s1)
 
 
 # ---------------------------------------------------------------- Sigma
