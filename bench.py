@@ -454,7 +454,7 @@ def _roofline(prof, cfg, npairs, steps, step_s):
         out.update(bound="tensor", peak=peak, peak_note=(
             f"TF32 x3: bf16 {'sustained' if sustained else 'burst'} {bf16_sus if sustained else bf16:.1f} TF/s "
             f"({which}) x nominal TF32/BF16 1.1/2.25, / 3 products"))
-        # the survey's minimum traffic of the chain kernels: V read once per launch (complex64)
+        # the minimum traffic of a chain launch: V read once (complex64)
         vbytes = 8.0 * npairs * cfg.naux * cfg.nao * cfg.nao
         out["algorithmic_bytes_per_launch"] = vbytes
         out["flop_per_algorithmic_byte"] = gf * 1e9 / nl / vbytes

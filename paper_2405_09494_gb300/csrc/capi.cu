@@ -367,7 +367,7 @@ extern "C" SGW_API sgw_status sgw_sync(sgw_ctx* c, sgw_stream stream) {
 // ---------------------------------------------------------------------------
 // a1: irrep basis
 // ---------------------------------------------------------------------------
-// tau reflection of P0 (the survey's reading C-5; Algorithm 3 loops tau to n_tau/2).  From
+// tau reflection of P0 (Algorithm 3 loops tau to n_tau/2; here without its time reversal).  From
 // Eq. (P0) with G(tau - beta) = -G(tau) and V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger,
 //     P0^q(tau) = P0^{-q}(beta - tau)^T   (auxiliary basis, every q, every tau).
 // On the Chebyshev roots beta - tau_j = tau_{n-1-j}.  In block coordinates, with U^k the rotated
@@ -851,7 +851,7 @@ sgw_status sgw::lower_from_upper(sgw_ctx* c, int which, double2* X, cudaStream_t
 }
 
 // G(tau) of Eq. (dyson) is Hermitian at every tau when H0, S, Sigma_HF and Sigma~(tau) are and the
-// fermionic set is closed under w -> -w (reading R-18): with c->herm the Dyson output is replaced
+// fermionic set is closed under w -> -w: with c->herm the Dyson output is replaced
 // by its Hermitian part, which changes it only at the rounding level and keeps the loop on the
 // Hermitian subspace (an anti-Hermitian rounding component is otherwise free to grow from pass to
 // pass in an undamped loop).

@@ -39,7 +39,7 @@ def test_tensor_class_is_tensor_bound_with_the_sustained_peak_in_long_steps(benc
     assert long_step["peak"] == pytest.approx(bf16_sus * 1.1 / 2.25 / 3)
     assert short_step["peak"] == pytest.approx(bf16 * 1.1 / 2.25 / 3)
     assert long_step["frac"] >= short_step["frac"]
-    # the survey's minimum bytes of a chain launch: V once, complex64
+    # the minimum bytes of a chain launch: V once, complex64
     assert long_step["algorithmic_bytes_per_launch"] == pytest.approx(8.0 * 512 * 300 * 52 * 52)
 
 

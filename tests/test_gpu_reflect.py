@@ -1,4 +1,4 @@
-"""The tau reflection of P0 (reading C-5 of the survey; Algorithm 3 loops tau to n_tau/2).
+"""The tau reflection of P0 (Algorithm 3 loops tau to n_tau/2; here without its time reversal).
 
 From Eq. (P0) with antiperiodicity and the Hermitian pairing of V, P0^q(tau) = P0^{-q}(beta - tau)^T;
 on the Chebyshev nodes beta - tau_j = tau_{n-1-j}.  The library contracts the first ceil(n_tau / 2)
