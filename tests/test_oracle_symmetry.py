@@ -156,6 +156,27 @@ def test_synthetic_inputs_are_covariant_under_the_oracle_representation():
                 assert np.abs(rot - sysm.V(a, b)).max() < 1e-12
 
 
+@pytest.mark.parametrize("name", ["t1", "c1"])
+def test_synthetic_inputs_are_seeded_hermitian_and_paired(name):
+    """The input generator's promises that the method relies on: two instances draw the same inputs;
+    H0 and S are Hermitian, and S is positive definite; and V^{k2,k1}_Q = (V^{k1,k2}_Q)^dagger for
+    every Q.  That pairing is what makes P0^q(tau) = P0^{-q}(beta - tau)^T, the relation the tau
+    reflection uses."""
+    from paper_2405_09494_gb300 import configs, synth
+
+    cfg = configs.get(name)
+    a, b = synth.System(cfg), synth.System(cfg)
+    assert np.array_equal(a.H0, b.H0) and np.array_equal(a.S, b.S)
+    for k in range(cfg.nkpts):
+        assert np.abs(a.H0[k] - a.H0[k].conj().T).max() < 1e-14
+        assert np.abs(a.S[k] - a.S[k].conj().T).max() < 1e-14
+        assert np.linalg.eigvalsh(a.S[k]).min() > 0
+    for k1, k2 in ((0, 1), (2, 5), (3, 3), (7, 4)):
+        V12, V21 = a.V(k1, k2), a.V(k2, k1)
+        assert np.array_equal(V12, b.V(k1, k2))
+        assert np.abs(V21 - V12.conj().transpose(0, 2, 1)).max() < 1e-13 * np.abs(V12).max()
+
+
 def test_oracle_self_energy_and_polarization_are_equivariant():
     """Sigma^{alpha k} = O Sigma^k O^dagger and P0^{alpha q} = O_aux P0^q O_aux^dagger (Eqs. (mat_rot), (prot))."""
     from oracle import grid, gw
