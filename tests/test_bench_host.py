@@ -1,5 +1,6 @@
 """Host logic of bench.py (no GPU): the roofline a kernel class is reported against, the measured
-peaks, the oracle's core count and which workloads get a whole oracle pass."""
+peaks, the oracle's core count, which workloads get a whole oracle pass, and the reference arm
+launched as two ranks."""
 import importlib.util
 import json
 import os
@@ -67,3 +68,27 @@ def test_oracle_core_count_follows_the_blas_thread_variables(bench, monkeypatch)
     monkeypatch.setenv("OMP_NUM_THREADS", "6")
     monkeypatch.setenv("OPENBLAS_NUM_THREADS", "4")
     assert bench.blas_threads() == 4
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0(tmp_path):
+    """`bench.py --impl reference` launched as two ranks (the driver's multi-GPU launch): rank 0
+    times the oracle on workload c1 and prints the one JSON line; rank 1 exits 0 without work."""
+    import socket
+    import subprocess
+    import sys
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus",
+           "2", "--config", "c1", "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run(cmd, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["config"]["name"] == "c1"
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["cores"] == 2
