@@ -325,6 +325,15 @@ SGW_API sgw_status sgw_host_grid(const sgw_params* params, double* tau, double* 
  * room for nkpts wedge points).  Any output but nwedge may be NULL. */
 SGW_API sgw_status sgw_host_symmetry(const sgw_params* params, const sgw_structure* st, int* nwedge, int* rep,
                                      int* ao_blocks, int* aux_blocks);
+/* Irrep dimension d of every block of sgw_host_symmetry, in the same zero-terminated row layout
+ * (ao_dims[nwedge][nao + 1], aux_dims[nwedge][naux + 1], host; rows need room for nkpts wedge
+ * points): in a partner-adapted basis a block of size s is d identical (s / d) x (s / d) copies
+ * (Sec. 3.4, the irreducible decomposition of the orbital representation).  d comes from the
+ * block's Dirac-character eigenvalues lambda_c (Eq. (dirac)): d^2 = h / sum_c |lambda_c|^2 / n_c
+ * over the classes c of the little co-group of order h.  A 0 marks a block whose vectors
+ * disagreed on d.  Any output but nwedge may be NULL. */
+SGW_API sgw_status sgw_host_irrep_dims(const sgw_params* params, const sgw_structure* st, int* nwedge, int* ao_dims,
+                                       int* aux_dims);
 
 /* ---- instrumentation (not part of the method) ---------------------------- */
 

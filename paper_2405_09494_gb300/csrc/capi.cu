@@ -2026,6 +2026,28 @@ extern "C" SGW_API sgw_status sgw_host_grid(const sgw_params* p, double* tau, do
   return SGW_OK;
 }
 
+extern "C" SGW_API sgw_status sgw_host_irrep_dims(const sgw_params* p, const sgw_structure* st, int* nwedge,
+                                                  int* ao_dims, int* aux_dims) {
+  if (!params_ok(p) || !st || !nwedge) return SGW_ERR_ARG;
+  sgw_ctx c;
+  host_ctx(p, c);
+  sgw_status s = build_symmetry(&c, st);
+  if (s != SGW_OK) return s;
+  *nwedge = c.nwedge;
+  for (int w = 0; w < c.nwedge; ++w) {
+    for (int fam = 0; fam < 2; ++fam) {
+      int* out = fam == 0 ? ao_dims : aux_dims;
+      if (!out) continue;
+      const Partition& P = fam == 0 ? c.part_ao[w] : c.part_aux[w];
+      int* row = out + (size_t)w * ((fam == 0 ? c.nao : c.naux) + 1);
+      int i = 0;
+      for (int d : P.dims) row[i++] = d;
+      row[i] = 0;
+    }
+  }
+  return SGW_OK;
+}
+
 extern "C" SGW_API sgw_status sgw_host_symmetry(const sgw_params* p, const sgw_structure* st, int* nwedge, int* rep,
                                                 int* ao_blocks, int* aux_blocks) {
   if (!params_ok(p) || !st || !nwedge) return SGW_ERR_ARG;

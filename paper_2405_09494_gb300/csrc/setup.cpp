@@ -541,11 +541,16 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
       const Basis& B = bas[b];
       struct Vec {
         double ev;
-        int shell;
+        int shell, dim;
         std::vector<cplx> v;  // over (x, m) of that shell
       };
+      struct Eig {
+        std::vector<double> ev;
+        std::vector<cplx> V;
+        std::vector<int> dim;
+      };
       std::vector<Vec> all;
-      std::map<int, std::pair<std::vector<double>, std::vector<cplx>>> by_l;
+      std::map<int, Eig> by_l;
       for (auto& kvp : B.D) {
         const int l = kvp.first, d = 2 * l + 1, ds = nat * d;
         // projective representation D^k(a) = e^{i k.v(a)} O^k(a) on the subspace of one shell of angular momentum l
@@ -564,6 +569,7 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
         // Dirac characters Omega_c = (n_c / h) sum_beta D(beta) D(gamma_c) D(beta)^dagger, and the
         // Hermitian combination H = sum_c a_c (Omega + Omega^dagger) + b_c i (Omega - Omega^dagger)
         std::vector<cplx> Hm((size_t)ds * ds, cplx(0, 0)), T1((size_t)ds * ds), Om((size_t)ds * ds);
+        std::vector<std::vector<cplx>> Oms(ncls);
         for (int cc = 0; cc < ncls; ++cc) {
           std::fill(Om.begin(), Om.end(), cplx(0, 0));
           const auto& Dg = Dm[reps[cc]];
@@ -582,6 +588,7 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
                 Om[(size_t)i * ds + j] += s * ((double)ncl[cc] / h);
               }
           }
+          Oms[cc] = Om;
           const double ac = std::sin(1.0 + 2.3 * cc) + 1.7, bc = std::cos(0.5 + 1.3 * cc);
           for (int i = 0; i < ds; ++i)
             for (int j = 0; j < ds; ++j) {
@@ -592,17 +599,36 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
         std::vector<cplx> V;
         std::vector<double> ev;
         host_jacobi(Hm, ds, V, ev);
-        by_l[l] = {ev, V};
+        // irrep dimension of each eigenvector: on an irrep subspace Omega_c acts as
+        // lambda_c = n_c chi(gamma_c) / d, |chi| is constant on a class (conjugation adds a phase
+        // in a projective representation), and sum_g |chi(g)|^2 = h, so
+        // d^2 = h / sum_c |lambda_c|^2 / n_c with lambda_c the Rayleigh quotient v^dagger Omega_c v
+        std::vector<int> dim(ds, 0);
+        for (int j = 0; j < ds; ++j) {
+          double sum = 0.0;
+          for (int cc = 0; cc < ncls; ++cc) {
+            cplx lam(0, 0);
+            for (int i = 0; i < ds; ++i) {
+              cplx t(0, 0);
+              for (int k2 = 0; k2 < ds; ++k2) t += Oms[cc][(size_t)i * ds + k2] * V[(size_t)k2 * ds + j];
+              lam += std::conj(V[(size_t)i * ds + j]) * t;
+            }
+            sum += std::norm(lam) / ncl[cc];
+          }
+          dim[j] = sum > 0.0 ? (int)std::lround(std::sqrt((double)h / sum)) : 0;
+        }
+        by_l[l] = {ev, V, dim};
       }
       for (size_t s = 0; s < B.shells.size(); ++s) {
         const int l = B.shells[s], d = 2 * l + 1, ds = nat * d;
-        const auto& evV = by_l[l];
+        const Eig& evV = by_l[l];
         for (int j = 0; j < ds; ++j) {
           Vec vv;
-          vv.ev = evV.first[j];
+          vv.ev = evV.ev[j];
           vv.shell = (int)s;
+          vv.dim = evV.dim[j];
           vv.v.resize(ds);
-          for (int i = 0; i < ds; ++i) vv.v[i] = evV.second[(size_t)i * ds + j];
+          for (int i = 0; i < ds; ++i) vv.v[i] = evV.V[(size_t)i * ds + j];
           all.push_back(vv);
         }
       }
@@ -620,6 +646,8 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
           P.sizes.push_back(col - start);
           start = col;
         }
+        if (col == start) P.dims.push_back(all[i].dim);
+        else if (P.dims.back() != all[i].dim) P.dims.back() = 0;
         const int s = all[i].shell, l = B.shells[s], d = 2 * l + 1;
         for (int x = 0; x < nat; ++x)
           for (int a = 0; a < d; ++a)

@@ -26,6 +26,9 @@ struct Partition {
   std::vector<int> isize;      // per index: size of its block
   std::vector<long long> doff; // per index: packed offset of its block
   long long elems = 0;
+  // per block: dimension d of its irrep; in a partner-adapted basis the block is d identical
+  // m x m copies, m = size / d (0: the block's vectors disagreed on d)
+  std::vector<int> dims;
 };
 
 // Item of a block-diagonal multiply (see bd_mult).

@@ -27,7 +27,7 @@ EXPORTS = [
     "sgw_g0", "sgw_polarization", "sgw_screened_interaction", "sgw_self_energy", "sgw_hartree_fock", "sgw_dyson",
     "sgw_energy", "sgw_iterate", "sgw_unfold", "sgw_host_grid", "sgw_host_symmetry", "sgw_profile_enable",
     "sgw_profile_read", "sgw_screened_interaction_noalloc", "sgw_set_wait_limit", "sgw_polarization_pairs",
-    "sgw_self_energy_pairs",
+    "sgw_self_energy_pairs", "sgw_host_irrep_dims",
 ]
 
 
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "sgw_unfold": ([vp, i, i, vp, vp, vp], i),
         "sgw_host_grid": ([ctypes.POINTER(Params), vp, vp, vp, vp, vp], i),
         "sgw_host_symmetry": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp, vp], i),
+        "sgw_host_irrep_dims": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp], i),
         "sgw_screened_interaction_noalloc": ([vp, vp, vp, vp], i),
         "sgw_profile_enable": ([vp, i], i),
         "sgw_set_wait_limit": ([vp, ctypes.c_ulonglong], i),
@@ -352,6 +353,23 @@ def sgw_host_grid(nk, nao, naux, ntau, mats_f, mats_b, beta, n_elec=1.0):
     _check(load_library().sgw_host_grid(ctypes.byref(p), tau.ctypes.data, TF.ctypes.data, TFb.ctypes.data,
                                         TB.ctypes.data, TBb.ctypes.data))
     return tau, TF, TFb, TB, TBb
+
+
+def sgw_host_irrep_dims(nk, nao, naux, lattice, positions, rotations, translations, ao_shells, aux_shells):
+    """Host-only: the irrep dimension d of every block of sgw_host_symmetry, per wedge point (ao, aux)."""
+    import numpy as np
+
+    p = _params(nk, nao, naux, 2, [0, 1], [0, 1], 1.0, 1.0)
+    st = _structure(lattice, positions, rotations, translations, ao_shells, aux_shells)
+    Nk = nk[0] * nk[1] * nk[2]
+    nw = ctypes.c_int()
+    ao = np.zeros((Nk, nao + 1), np.int32)
+    ax = np.zeros((Nk, naux + 1), np.int32)
+    _check(load_library().sgw_host_irrep_dims(ctypes.byref(p), ctypes.byref(st), ctypes.byref(nw), ao.ctypes.data,
+                                              ax.ctypes.data))
+    n = nw.value
+    dims = lambda row: [int(x) for x in row[: list(row).index(0)]]  # noqa: E731
+    return [dims(ao[w]) for w in range(n)], [dims(ax[w]) for w in range(n)]
 
 
 def sgw_host_symmetry(nk, nao, naux, lattice, positions, rotations, translations, ao_shells, aux_shells):

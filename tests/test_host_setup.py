@@ -9,6 +9,8 @@
   partition covers the basis.
 * Every workload's Matsubara sets are sorted and mirror-symmetric (the Hermitian shortcuts and the
   half-frequency W solve depend on it).
+* The irrep dimension of every block, from the Dirac-character eigenvalues, equals the eigenvalue
+  multiplicity of a group-averaged random operator on the oracle's block.
 """
 import json
 import os
@@ -158,3 +160,46 @@ def test_every_workload_frequency_set_is_sorted_and_mirror_symmetric(name):
     assert all(mf[len(mf) - 1 - i] == -mf[i] - 1 for i in range(len(mf)))
     assert all(mb[len(mb) - 1 - i] == -mb[i] for i in range(len(mb)))
     assert 0 in mb
+
+
+@pytest.mark.parametrize("structure", ["rocksalt", "diamond"])
+def test_library_irrep_dims_match_the_multiplicity_of_an_invariant_operator(structure):
+    """The library's irrep dimension d of every block comes from its Dirac-character eigenvalues.
+    Two things must hold at every wedge point of the 4x4x4 mesh.  d divides the block size.  And,
+    matched by block size, d equals the eigenvalue multiplicity of a random Hermitian operator
+    averaged over the little group and restricted to the oracle's block.  By Schur's lemma that
+    operator is I_d (x) A on the block's d copies."""
+    sgw = _lib()
+    from oracle import symmetry as sy
+    from paper_2405_09494_gb300 import synth
+
+    ops = synth.space_group(structure)
+    pos = synth.atom_positions(structure)
+    aos, axs = (0, 1, 2), (0, 1, 2, 3, 4)
+    rot = np.stack([R for R, _ in ops])
+    tra = np.stack([v for _, v in ops])
+    nao = len(pos) * sum(2 * l + 1 for l in aos)
+    naux = len(pos) * sum(2 * l + 1 for l in axs)
+    nw, _, ao, ax = sgw.sgw_host_symmetry((4, 4, 4), nao, naux, synth.FCC, pos, rot, tra, aos, axs)
+    dao, dax = sgw.sgw_host_irrep_dims((4, 4, 4), nao, naux, synth.FCC, pos, rot, tra, aos, axs)
+    assert len(dao) == len(dax) == nw
+    rng = np.random.default_rng(5)
+    for shells, lib_sizes, lib_dims in ((aos, ao, dao), (axs, ax, dax)):
+        cr = sy.Crystal(synth.FCC, pos, ops, shells)
+        reps, _ = sy.stars(cr, (4, 4, 4))
+        for w, k in enumerate(reps):
+            assert len(lib_dims[w]) == len(lib_sizes[w]), (structure, w)
+            assert all(d > 0 and s % d == 0 for s, d in zip(lib_sizes[w], lib_dims[w])), (structure, w)
+            omegas, D, G = sy.dirac_characters(cr, (4, 4, 4), k)
+            U, sizes = sy.simultaneous_diagonalize(omegas, cr.n)
+            R = rng.standard_normal((cr.n, cr.n)) + 1j * rng.standard_normal((cr.n, cr.n))
+            R = R + R.conj().T
+            H = sum(D[g] @ R @ D[g].conj().T for g in G) / len(G)
+            pairs, st = [], 0
+            for sz in sizes:
+                B = U[:, st:st + sz]
+                ev = np.linalg.eigvalsh(B.conj().T @ H @ B)
+                distinct = 1 + int(np.sum(np.diff(ev) > 1e-8 * max(1.0, np.abs(ev).max())))
+                pairs.append((sz, sz // distinct))
+                st += sz
+            assert sorted(pairs) == sorted(zip(lib_sizes[w], lib_dims[w])), (structure, w, pairs)
