@@ -334,6 +334,15 @@ SGW_API sgw_status sgw_host_symmetry(const sgw_params* params, const sgw_structu
  * disagreed on d.  Any output but nwedge may be NULL. */
 SGW_API sgw_status sgw_host_irrep_dims(const sgw_params* params, const sgw_structure* st, int* nwedge, int* ao_dims,
                                        int* aux_dims);
+/* Partner-adapted bases of one family (family 0: orbitals, 1: auxiliary) at every wedge point:
+ * U[nwedge][n][n] interleaved complex (host, room for nkpts wedge points), column j a basis vector
+ * in the AO basis.  The blocks are those of sgw_host_symmetry, in the same order.  Within a block
+ * of irrep dimension d and size s = m d, column i m + a is partner i of copy a, so every
+ * operator that commutes with the little group's projective representation is I_d (x) A there
+ * (Sec. 3.4, Schur's lemma).  Blocks with d = 1 keep the basis of sgw_build_irrep_basis.  Not
+ * used by the device path. */
+SGW_API sgw_status sgw_host_partner_basis(const sgw_params* params, const sgw_structure* st, int family, int* nwedge,
+                                          double* U);
 
 /* ---- instrumentation (not part of the method) ---------------------------- */
 

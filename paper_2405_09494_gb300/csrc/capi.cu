@@ -2048,6 +2048,28 @@ extern "C" SGW_API sgw_status sgw_host_irrep_dims(const sgw_params* p, const sgw
   return SGW_OK;
 }
 
+extern "C" SGW_API sgw_status sgw_host_partner_basis(const sgw_params* p, const sgw_structure* st, int family,
+                                                     int* nwedge, double* U) {
+  if (!params_ok(p) || !st || !nwedge || (family != 0 && family != 1)) return SGW_ERR_ARG;
+  sgw_ctx c;
+  host_ctx(p, c);
+  c.want_partner = true;
+  sgw_status s = build_symmetry(&c, st);
+  if (s != SGW_OK) return s;
+  *nwedge = c.nwedge;
+  if (U) {
+    const size_t nn = (size_t)(family == 0 ? c.nao : c.naux) * (family == 0 ? c.nao : c.naux);
+    for (int w = 0; w < c.nwedge; ++w) {
+      const auto& X = c.partner_U[family][w];
+      for (size_t e = 0; e < nn; ++e) {
+        U[2 * ((size_t)w * nn + e)] = X[e].real();
+        U[2 * ((size_t)w * nn + e) + 1] = X[e].imag();
+      }
+    }
+  }
+  return SGW_OK;
+}
+
 extern "C" SGW_API sgw_status sgw_host_symmetry(const sgw_params* p, const sgw_structure* st, int* nwedge, int* rep,
                                                 int* ao_blocks, int* aux_blocks) {
   if (!params_ok(p) || !st || !nwedge) return SGW_ERR_ARG;

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <random>
 #include <set>
 
 #include "sgw_internal.h"
@@ -486,6 +487,127 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
     }
   };
 
+  // Partner-adapted basis of every block of the Dirac basis U (Sec. 3.4): a block of irrep dimension d
+  // and multiplicity m holds m copies of the irrep.  Gamma(g) = U_b^dagger D(g) U_b is the
+  // representation on the block.  A group-averaged random Hermitian operator
+  // A1 = (1/h) sum_g Gamma R1 Gamma^dagger commutes with it, so it is I_d (x) a on the copies:
+  // its eigenvalues come in m clusters of d, one cluster per copy.  A second averaged operator A2
+  // maps copy 1 onto copy a through T_a = C_a^dagger A2 C_1.  By Schur's lemma T_a is a scalar times
+  // a unitary W_a, and the basis C_a W_a of copy a transforms exactly as C_1 does.  The columns are
+  // ordered partner-major, (partner i, copy a) at i m + a, so every invariant operator reads I_d (x) A
+  // on the block.  A block with d = 1, an invalid d, or clusters not of size d keeps its Dirac basis.
+  auto partner_basis = [&](const Basis& B, const std::vector<cplx>& U, const Partition& P, const std::vector<int>& bstart,
+                           int w, int fam, int k, const std::vector<int>& little, auto&& kv, auto&& applyO) {
+    const int n = B.n, h = (int)little.size();
+    std::vector<cplx> Up(U);
+    std::vector<std::vector<cplx>> DU(h);
+    for (int i = 0; i < h; ++i) {
+      applyO(B, little[i], k, U, n, DU[i]);
+      const cplx e = kv(little[i]);
+      for (auto& z : DU[i]) z *= e;
+    }
+    std::mt19937_64 rng(0x5eed0000ULL + 131ULL * w + 7ULL * fam);
+    auto unif = [&]() { return (double)(rng() >> 11) * (1.0 / 9007199254740992.0) - 0.5; };
+    for (size_t bi = 0; bi < P.sizes.size(); ++bi) {
+      const int sz = P.sizes[bi], d = P.dims[bi], b0 = bstart[bi];
+      if (d <= 1 || sz % d != 0) continue;
+      const int m = sz / d;
+      std::vector<std::vector<cplx>> Gm(h, std::vector<cplx>((size_t)sz * sz));
+      for (int i = 0; i < h; ++i)
+        for (int r = 0; r < sz; ++r)
+          for (int cc = 0; cc < sz; ++cc) {
+            cplx acc(0, 0);
+            for (int t = 0; t < n; ++t) acc += std::conj(U[(size_t)t * n + b0 + r]) * DU[i][(size_t)t * n + b0 + cc];
+            Gm[i][(size_t)r * sz + cc] = acc;
+          }
+      auto average = [&](const std::vector<cplx>& R) {
+        std::vector<cplx> A((size_t)sz * sz, cplx(0, 0)), T((size_t)sz * sz);
+        for (int i = 0; i < h; ++i) {
+          const auto& Gg = Gm[i];
+          for (int r = 0; r < sz; ++r)
+            for (int cc = 0; cc < sz; ++cc) {
+              cplx acc(0, 0);
+              for (int t = 0; t < sz; ++t) acc += Gg[(size_t)r * sz + t] * R[(size_t)t * sz + cc];
+              T[(size_t)r * sz + cc] = acc;
+            }
+          for (int r = 0; r < sz; ++r)
+            for (int cc = 0; cc < sz; ++cc) {
+              cplx acc(0, 0);
+              for (int t = 0; t < sz; ++t) acc += T[(size_t)r * sz + t] * std::conj(Gg[(size_t)cc * sz + t]);
+              A[(size_t)r * sz + cc] += acc;
+            }
+        }
+        for (auto& z : A) z /= (double)h;
+        return A;
+      };
+      std::vector<cplx> R1((size_t)sz * sz), R2((size_t)sz * sz);
+      for (int r = 0; r < sz; ++r)
+        for (int cc = 0; cc <= r; ++cc) {
+          const cplx z(unif(), r == cc ? 0.0 : unif());
+          R1[(size_t)r * sz + cc] = z;
+          R1[(size_t)cc * sz + r] = std::conj(z);
+        }
+      for (auto& z : R2) z = cplx(unif(), unif());
+      std::vector<cplx> A1 = average(R1), A2 = average(R2);
+      std::vector<cplx> V;
+      std::vector<double> ev;
+      host_jacobi(A1, sz, V, ev);
+      std::vector<int> ord(sz);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::sort(ord.begin(), ord.end(), [&](int a, int bb) { return ev[a] < ev[bb]; });
+      double scale = 0.0;
+      for (double e : ev) scale = std::max(scale, std::fabs(e));
+      bool ok = true;
+      for (int a = 0; a < m && ok; ++a) {  // clusters of exactly d, separated from their neighbours
+        const double lo = ev[ord[a * d]], hi = ev[ord[a * d + d - 1]];
+        ok = hi - lo <= 1e-9 * scale && (a == 0 || lo - ev[ord[a * d - 1]] > 1e-7 * scale);
+      }
+      if (!ok) continue;
+      // C[a] column j = V[:, ord[a d + j]]; T_a = C_a^dagger A2 C_1; W_a = T_a / sqrt(tr(T^dagger T) / d)
+      std::vector<cplx> blk((size_t)sz * sz, cplx(0, 0));  // new basis in block coordinates, column i m + a
+      for (int a = 0; a < m; ++a) {
+        std::vector<cplx> W((size_t)d * d, cplx(0, 0));
+        if (a == 0) {
+          for (int i = 0; i < d; ++i) W[(size_t)i * d + i] = 1.0;
+        } else {
+          std::vector<cplx> A2C1((size_t)sz * d, cplx(0, 0));
+          for (int r = 0; r < sz; ++r)
+            for (int j = 0; j < d; ++j) {
+              cplx acc(0, 0);
+              for (int t = 0; t < sz; ++t) acc += A2[(size_t)r * sz + t] * V[(size_t)t * sz + ord[j]];
+              A2C1[(size_t)r * d + j] = acc;
+            }
+          double nrm = 0.0;
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+              cplx acc(0, 0);
+              for (int r = 0; r < sz; ++r) acc += std::conj(V[(size_t)r * sz + ord[a * d + i]]) * A2C1[(size_t)r * d + j];
+              W[(size_t)i * d + j] = acc;
+              nrm += std::norm(acc);
+            }
+          nrm = std::sqrt(nrm / d);
+          if (!(nrm > 1e-12 * std::max(1.0, scale))) { ok = false; break; }
+          for (auto& z : W) z /= nrm;
+        }
+        // copy a's new partner i = sum_j C_a[:, j] W[j][i]
+        for (int i = 0; i < d; ++i)
+          for (int r = 0; r < sz; ++r) {
+            cplx acc(0, 0);
+            for (int j = 0; j < d; ++j) acc += V[(size_t)r * sz + ord[a * d + j]] * W[(size_t)j * d + i];
+            blk[(size_t)r * sz + (size_t)i * m + a] = acc;
+          }
+      }
+      if (!ok) continue;
+      for (int t = 0; t < n; ++t)
+        for (int col = 0; col < sz; ++col) {
+          cplx acc(0, 0);
+          for (int r = 0; r < sz; ++r) acc += U[(size_t)t * n + b0 + r] * blk[(size_t)r * sz + col];
+          Up[(size_t)t * n + b0 + col] = acc;
+        }
+    }
+    return Up;
+  };
+
   // irrep bases at the wedge points
   std::vector<std::vector<cplx>> Uw[2];
   c->part_ao.assign(c->nwedge, Partition());
@@ -678,6 +800,10 @@ sgw_status build_symmetry(sgw_ctx* c, const sgw_structure* st) {
       P.isize = vsize;
       (b == 0 ? c->part_ao : c->part_aux)[w] = P;
       Uw[b][w] = U;
+      if (c->want_partner) {
+        if (c->partner_U[b].size() != (size_t)c->nwedge) c->partner_U[b].assign(c->nwedge, {});
+        c->partner_U[b][w] = partner_basis(B, U, P, bstart, w, b, k, little, kv, apply_O);
+      }
     }
   }
   // packed offsets

@@ -241,6 +241,10 @@ struct sgw_ctx {
   int max_ao_block = 0, max_aux_block = 0;
   double2 *d_Uao = nullptr, *d_Uaux = nullptr;  // [Nk][n][n]
   std::vector<sgw::cplx> hostU[2];                // host copies, freed after upload
+  // partner-adapted bases of the wedge points ([nwedge][n x n] per family), built by
+  // build_symmetry only when want_partner is set (host-only query; the GPU path does not use them)
+  bool want_partner = false;
+  std::vector<std::vector<sgw::cplx>> partner_U[2];
   int *d_ao_start = nullptr, *d_ao_size = nullptr, *d_aux_start = nullptr, *d_aux_size = nullptr;
   long long *d_ao_doff = nullptr, *d_aux_doff = nullptr;
   // chunked unit tables of the orbital (0) and auxiliary (1) partitions, per wedge point

@@ -27,7 +27,7 @@ EXPORTS = [
     "sgw_g0", "sgw_polarization", "sgw_screened_interaction", "sgw_self_energy", "sgw_hartree_fock", "sgw_dyson",
     "sgw_energy", "sgw_iterate", "sgw_unfold", "sgw_host_grid", "sgw_host_symmetry", "sgw_profile_enable",
     "sgw_profile_read", "sgw_screened_interaction_noalloc", "sgw_set_wait_limit", "sgw_polarization_pairs",
-    "sgw_self_energy_pairs", "sgw_host_irrep_dims",
+    "sgw_self_energy_pairs", "sgw_host_irrep_dims", "sgw_host_partner_basis",
 ]
 
 
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "sgw_host_grid": ([ctypes.POINTER(Params), vp, vp, vp, vp, vp], i),
         "sgw_host_symmetry": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp, vp], i),
         "sgw_host_irrep_dims": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), ctypes.POINTER(i), vp, vp], i),
+        "sgw_host_partner_basis": ([ctypes.POINTER(Params), ctypes.POINTER(Structure), i, ctypes.POINTER(i), vp], i),
         "sgw_screened_interaction_noalloc": ([vp, vp, vp, vp], i),
         "sgw_profile_enable": ([vp, i], i),
         "sgw_set_wait_limit": ([vp, ctypes.c_ulonglong], i),
@@ -370,6 +371,21 @@ def sgw_host_irrep_dims(nk, nao, naux, lattice, positions, rotations, translatio
     n = nw.value
     dims = lambda row: [int(x) for x in row[: list(row).index(0)]]  # noqa: E731
     return [dims(ao[w]) for w in range(n)], [dims(ax[w]) for w in range(n)]
+
+
+def sgw_host_partner_basis(nk, nao, naux, lattice, positions, rotations, translations, ao_shells, aux_shells, family):
+    """Host-only: partner-adapted bases [nwedge][n][n] (complex) of one family (0 orbitals, 1 auxiliary)."""
+    import numpy as np
+
+    p = _params(nk, nao, naux, 2, [0, 1], [0, 1], 1.0, 1.0)
+    st = _structure(lattice, positions, rotations, translations, ao_shells, aux_shells)
+    Nk = nk[0] * nk[1] * nk[2]
+    n = nao if family == 0 else naux
+    nw = ctypes.c_int()
+    U = np.zeros((Nk, n, n), np.complex128)
+    _check(load_library().sgw_host_partner_basis(ctypes.byref(p), ctypes.byref(st), int(family), ctypes.byref(nw),
+                                                 U.ctypes.data))
+    return U[: nw.value]
 
 
 def sgw_host_symmetry(nk, nao, naux, lattice, positions, rotations, translations, ao_shells, aux_shells):

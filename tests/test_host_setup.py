@@ -11,6 +11,7 @@
   half-frequency W solve depend on it).
 * The irrep dimension of every block, from the Dirac-character eigenvalues, equals the eigenvalue
   multiplicity of a group-averaged random operator on the oracle's block.
+* In the partner-adapted bases every invariant operator is I_d (x) A on each block.
 """
 import json
 import os
@@ -203,3 +204,51 @@ def test_library_irrep_dims_match_the_multiplicity_of_an_invariant_operator(stru
                 pairs.append((sz, sz // distinct))
                 st += sz
             assert sorted(pairs) == sorted(zip(lib_sizes[w], lib_dims[w])), (structure, w, pairs)
+
+
+@pytest.mark.parametrize("structure", ["rocksalt", "diamond"])
+def test_partner_basis_puts_invariant_operators_in_identical_copies(structure):
+    """The partner-adapted bases (sgw_host_partner_basis) at every wedge point of a 4x4x4 mesh, for
+    both families, are unitary.  In them, an operator commuting with the oracle's projective
+    representation of the little group (a group-averaged random Hermitian operator) is block
+    diagonal over the library's blocks.  On a block of irrep dimension d and multiplicity m it reads
+    I_d (x) A: the d diagonal m x m blocks are equal, the rest vanish (Schur's lemma)."""
+    sgw = _lib()
+    from oracle import symmetry as sy
+    from paper_2405_09494_gb300 import synth
+
+    ops = synth.space_group(structure)
+    pos = synth.atom_positions(structure)
+    aos, axs = (0, 1, 2), (0, 1, 2, 3, 4)
+    rot = np.stack([R for R, _ in ops])
+    tra = np.stack([v for _, v in ops])
+    nao = len(pos) * sum(2 * l + 1 for l in aos)
+    naux = len(pos) * sum(2 * l + 1 for l in axs)
+    args = ((4, 4, 4), nao, naux, synth.FCC, pos, rot, tra, aos, axs)
+    _, _, ao, ax = sgw.sgw_host_symmetry(*args)
+    dao, dax = sgw.sgw_host_irrep_dims(*args)
+    rng = np.random.default_rng(9)
+    for fam, shells, sizes, dims in ((0, aos, ao, dao), (1, axs, ax, dax)):
+        U = sgw.sgw_host_partner_basis(*args, fam)
+        cr = sy.Crystal(synth.FCC, pos, ops, shells)
+        reps, _ = sy.stars(cr, (4, 4, 4))
+        assert U.shape[0] == len(reps)
+        for w, k in enumerate(reps):
+            n = cr.n
+            assert np.abs(U[w].conj().T @ U[w] - np.eye(n)).max() < 1e-12, (structure, fam, w)
+            _, D, G = sy.dirac_characters(cr, (4, 4, 4), k)
+            R = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+            H = sum(D[g] @ (R + R.conj().T) @ D[g].conj().T for g in G) / len(G)
+            X = U[w].conj().T @ H @ U[w]
+            scale = np.abs(X).max()
+            st = 0
+            for sz, d in zip(sizes[w], dims[w]):
+                m = sz // d
+                assert np.abs(X[st:st + sz, st + sz:]).max(initial=0.0) < 1e-11 * scale
+                B = X[st:st + sz, st:st + sz]
+                for i in range(d):
+                    for j in range(d):
+                        ref = B[:m, :m] if i == j else 0.0
+                        err = np.abs(B[i * m:(i + 1) * m, j * m:(j + 1) * m] - ref).max()
+                        assert err < 1e-11 * scale, (structure, fam, w, sz, d, i, j, err / scale)
+                st += sz
